@@ -1,0 +1,244 @@
+"""Seeded synthetic sparse tensors and factor initialisations.
+
+This module is shared by the CPU oracle's tests and the CUDA path's tests and
+benchmark. It holds NO arithmetic of the method (no encoding, no MTTKRP, no
+ALS): only counter-based random numbers and the distributions built on them.
+
+Random numbers: SplitMix64 (Steele, Lea & Flood, 2014) in counter mode. The
+draw for (seed, tag, index) is ``mix64(base + (index + 1) * GAMMA)`` with
+``base = mix64(seed * GAMMA + tag)``; so every array is deterministic and can
+be generated in any order or in parallel.
+
+Distributions:
+* uniform(0,1]   = ((x >> 11) + 1) * 2^-53.
+* uniform label on [0, I) = floor(((x >> 11) * 2^-53) * I).
+* Zipf(alpha) on [0, I): P(k) proportional to (k+1)^-alpha, by inverse CDF
+  (binary search in an FP64 cumulative table).
+* lognormal(0,1) = exp(z), z from Box-Muller on two uniform(0,1] draws, FP64,
+  then rounded to FP32.
+* "shuffled" labels: a seeded per-mode permutation of [0, I) (the paper's
+  shuffled experiments, Sec. 4.1.3).
+* Distinct coordinates: draws are taken in counter order and the first
+  occurrence of each coordinate tuple is kept until nnz tuples are collected.
+
+The tensors stand in for the FROSTT tensors of the paper's Table I (not
+available here): power-law modes, a short time-like mode, hyper-sparse dims.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+TAG_COORD = 0x100   # + mode
+TAG_VAL = 0x200
+TAG_VAL2 = 0x201
+TAG_FACTOR = 0x300
+TAG_LABELS = 0x400  # + mode
+
+
+def mix64(z: np.ndarray) -> np.ndarray:
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream(seed: int, tag: int, idx: np.ndarray) -> np.ndarray:
+    """Counter-mode SplitMix64 draws for indices idx (uint64)."""
+    with np.errstate(over="ignore"):
+        base = mix64(np.array([(seed * 0x9E3779B97F4A7C15 + tag) & (2**64 - 1)], dtype=np.uint64))[0]
+        idx = np.asarray(idx, dtype=np.uint64)
+        return mix64(base + (idx + np.uint64(1)) * GAMMA)
+
+
+def uniform01(x: np.ndarray) -> np.ndarray:
+    """uniform(0,1] from 64-bit draws."""
+    return ((x >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+
+
+def uniform_label(x: np.ndarray, I: int) -> np.ndarray:
+    u = (x >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return np.minimum((u * I).astype(np.int64), I - 1).astype(np.uint32)
+
+
+def zipf_table(I: int, alpha: float) -> np.ndarray:
+    w = np.arange(1, I + 1, dtype=np.float64) ** (-float(alpha))
+    return np.cumsum(w)
+
+
+def zipf_label(x: np.ndarray, cdf: np.ndarray) -> np.ndarray:
+    t = uniform01(x) * cdf[-1]
+    k = np.searchsorted(cdf, t, side="left")
+    return np.minimum(k, len(cdf) - 1).astype(np.uint32)
+
+
+def label_permutation(seed: int, mode: int, I: int) -> np.ndarray:
+    keys = stream(seed, TAG_LABELS + mode, np.arange(I, dtype=np.uint64))
+    return np.argsort(keys, kind="stable").astype(np.uint32)
+
+
+@dataclass
+class TensorSpec:
+    """A synthetic sparse tensor: dims, nnz, per-mode label distribution."""
+    name: str
+    dims: tuple
+    nnz: int
+    dists: tuple            # per mode: ("uniform",) or ("zipf", alpha)
+    values: str = "uniform"  # "uniform" (U(0,1]) or "lognormal"
+    value_dtype: str = "f32"  # "f32" or "f64"
+    seed: int = 1
+    shuffle: bool = False
+    distinct: bool = True
+    extra: dict = field(default_factory=dict)
+
+
+def _draw_coords(spec: TensorSpec, lo: int, hi: int, tables) -> np.ndarray:
+    idx = np.arange(lo, hi, dtype=np.uint64)
+    N = len(spec.dims)
+    out = np.empty((N, hi - lo), dtype=np.uint32)
+    for n in range(N):
+        x = stream(spec.seed, TAG_COORD + n, idx)
+        d = spec.dists[n]
+        if d[0] == "zipf":
+            lab = zipf_label(x, tables[n])
+        elif d[0] == "uniform":
+            lab = uniform_label(x, int(spec.dims[n]))
+        else:
+            raise ValueError(f"unknown distribution {d}")
+        if spec.shuffle:
+            lab = tables[N + n][lab]
+        out[n] = lab
+    return out
+
+
+def _dedup_keys(coords: np.ndarray, dims) -> list:
+    """Split the modes into groups whose mixed-radix products fit in uint64
+    and return one uint64 key per group (most significant group first)."""
+    groups, cur, prod = [], [], 1
+    for n, I in enumerate(dims):
+        if prod * int(I) >= 2 ** 64:
+            groups.append(cur)
+            cur, prod = [], 1
+        cur.append(n)
+        prod *= int(I)
+    groups.append(cur)
+    keys = []
+    for g in groups:
+        k = np.zeros(coords.shape[1], dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            for n in g:
+                k = k * np.uint64(int(dims[n])) + coords[n].astype(np.uint64)
+        keys.append(k)
+    return keys
+
+
+def make_coords(spec: TensorSpec) -> np.ndarray:
+    N = len(spec.dims)
+    tables = []
+    for n in range(N):
+        d = spec.dists[n]
+        tables.append(zipf_table(int(spec.dims[n]), d[1]) if d[0] == "zipf" else None)
+    if spec.shuffle:
+        for n in range(N):
+            tables.append(label_permutation(spec.seed, n, int(spec.dims[n])))
+    if not spec.distinct:
+        return _draw_coords(spec, 0, spec.nnz, tables)
+    M = int(spec.nnz * 1.25) + 1024
+    for _ in range(40):
+        c = _draw_coords(spec, 0, M, tables)
+        keys = _dedup_keys(c, spec.dims)
+        order = np.lexsort(tuple(reversed(keys))) if len(keys) > 1 else np.argsort(keys[0], kind="stable")
+        dup = np.ones(M, dtype=bool)
+        for k in keys:
+            ks = k[order]
+            dup[1:] &= ks[1:] == ks[:-1]
+        dup[0] = False
+        first = np.ones(M, dtype=bool)
+        first[order[dup]] = False
+        kept = np.nonzero(first)[0]
+        if kept.shape[0] >= spec.nnz:
+            return np.ascontiguousarray(c[:, kept[:spec.nnz]])
+        M = int(M * 1.6)
+    raise ValueError(f"{spec.name}: could not draw {spec.nnz} distinct coordinates")
+
+
+def make_values(spec: TensorSpec) -> np.ndarray:
+    idx = np.arange(spec.nnz, dtype=np.uint64)
+    u1 = uniform01(stream(spec.seed, TAG_VAL, idx))
+    if spec.values == "uniform":
+        v = u1
+    elif spec.values == "lognormal":
+        u2 = uniform01(stream(spec.seed, TAG_VAL2, idx))
+        v = np.exp(np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2))
+    elif spec.values.startswith("int"):
+        # "int:a:b" -> integers uniform in [a, b] (exact-arithmetic cases)
+        _, a, b = spec.values.split(":")
+        a, b = int(a), int(b)
+        v = (a + np.minimum((u1 * (b - a + 1)).astype(np.int64), b - a)).astype(np.float64)
+    else:
+        raise ValueError(spec.values)
+    return v.astype(np.float32) if spec.value_dtype == "f32" else v.astype(np.float64)
+
+
+def make_tensor(spec: TensorSpec):
+    """Returns (coords (N, nnz) uint32 SoA, vals (nnz,) f32/f64)."""
+    return make_coords(spec), make_values(spec)
+
+
+def init_factors(dims, R: int, seed: int = 0, dtype=np.float64, kind: str = "uniform"):
+    """Factor initialisation: uniform(0,1] drawn in order (mode k, row i,
+    column r) from one counter stream; FP64, then rounded to dtype.
+    kind="int:a:b" draws integers in [a, b] instead (exact cases)."""
+    out, off = [], 0
+    for I in dims:
+        idx = np.arange(off, off + int(I) * R, dtype=np.uint64)
+        u = uniform01(stream(seed, TAG_FACTOR, idx))
+        if kind.startswith("int"):
+            _, a, b = kind.split(":")
+            a, b = int(a), int(b)
+            u = (a + np.minimum((u * (b - a + 1)).astype(np.int64), b - a)).astype(np.float64)
+        out.append(u.reshape(int(I), R).astype(dtype))
+        off += int(I) * R
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Named workloads (the sizes the paper's workloads are stood in by)
+# ----------------------------------------------------------------------------
+WORKLOADS = {
+    # plain FP64 CP-ALS: 1000^3, 1M uniform distinct coords, U(0,1] values
+    "uniform3d-1000x1000x1000-1M": dict(
+        spec=TensorSpec("uniform3d-1000x1000x1000-1M", (1000, 1000, 1000), 1_000_000,
+                        (("uniform",),) * 3, values="uniform", value_dtype="f64", seed=1),
+        R=16, iters=10, factor_dtype="f64"),
+    # skewed 3-mode: Zipf 1.2 on every mode, lognormal FP32 values
+    "zipf3d-200Kx200Kx5K-50M": dict(
+        spec=TensorSpec("zipf3d-200Kx200Kx5K-50M", (200_000, 200_000, 5_000), 50_000_000,
+                        (("zipf", 1.2),) * 3, values="lognormal", value_dtype="f32", seed=2),
+        R=32, iters=25, factor_dtype="f32"),
+    # 4-mode with a short time-like mode
+    "zipf4d-5Mx1Mx100Kx24-150M": dict(
+        spec=TensorSpec("zipf4d-5Mx1Mx100Kx24-150M", (5_000_000, 1_000_000, 100_000, 24),
+                        150_000_000, (("zipf", 1.1),) * 3 + (("uniform",),),
+                        values="uniform", value_dtype="f32", seed=3),
+        R=64, iters=10, factor_dtype="f32"),
+    # 5-mode hyper-sparse
+    "zipf5d-10Mx10Mx1Mx1Kx100-100M": dict(
+        spec=TensorSpec("zipf5d-10Mx10Mx1Mx1Kx100-100M", (10_000_000, 10_000_000, 1_000_000, 1000, 100),
+                        100_000_000, (("zipf", 1.3),) * 2 + (("uniform",),) * 3,
+                        values="uniform", value_dtype="f32", seed=4),
+        R=16, iters=10, factor_dtype="bf16"),
+}
+
+
+def scaled(spec: TensorSpec, nnz: int, dims=None, name: str | None = None) -> TensorSpec:
+    """The same recipe at a smaller size (for parity cases)."""
+    return TensorSpec(name or f"{spec.name}@{nnz}", tuple(dims or spec.dims), nnz, spec.dists,
+                      spec.values, spec.value_dtype, spec.seed, spec.shuffle, spec.distinct)
