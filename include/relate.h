@@ -1,0 +1,228 @@
+/*
+ * relate.h -- C ABI of the GB300-native sparse MTTKRP / CP-ALS library.
+ *
+ * The library implements the hot path of "ReLATE: Accelerating Tensor
+ * Decomposition via Safe and Efficient Learning of Sparse Encodings"
+ * (arXiv 2509.00280): a linearized sparse-tensor encoding (Sec. 3.3), the
+ * mode-n MTTKRP over it (Sec. 2.2, Fig. 2), and CP-ALS around it (Sec. 2.2,
+ * the decomposition the paper accelerates; the ALS itself is the standard
+ * Kolda-Bader algorithm the paper cites).
+ *
+ * Conventions
+ *  - Modes are 0-based: the paper's mode n = 1..N is mode n-1 here.
+ *  - Coordinates are uint32, structure-of-arrays: coords[m * nnz + e] is the
+ *    mode-m index of nonzero e.
+ *  - A factor matrix A_k (the paper's C^(k), F = R columns) is I_k x R,
+ *    row-major with row stride R elements, in the handle's factor dtype.
+ *  - All pointers named "device" must be CUDA device memory of the current
+ *    device; "host" pointers are ordinary host memory.
+ *  - Streams are cudaStream_t passed as void*; NULL = the legacy default stream.
+ *  - Every call returns RELATE_OK (0) or a negative relate_status_t. The
+ *    message of the last failure is available from relate_last_error().
+ *  - Calls on one handle must not run concurrently from several host threads.
+ */
+#ifndef RELATE_H
+#define RELATE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RELATE_MAX_MODES 8
+#define RELATE_MAX_RANK 64
+#define RELATE_MAX_KEY_BITS 128
+
+typedef enum {
+    RELATE_OK = 0,
+    RELATE_ERR_INVALID_ARG = -1,        /* bad nmodes, dims, R, mode, pointer or dtype */
+    RELATE_ERR_BAD_BIT_ORDER = -2,      /* bit order breaks the masking rule (Alg. 1) */
+    RELATE_ERR_KEY_TOO_WIDE = -3,       /* l(p) > 128 */
+    RELATE_ERR_COORD_OUT_OF_RANGE = -4, /* some i_n >= I_n (found on the device) */
+    RELATE_ERR_OOM = -5,                /* device allocation failed */
+    RELATE_ERR_NOT_PD = -6,             /* normal-equations matrix not positive definite
+                                           even after the ridge retry */
+    RELATE_ERR_TIMEOUT = -7,            /* a bounded device wait ran out */
+    RELATE_ERR_CUDA = -8,               /* CUDA runtime error; see relate_last_error() */
+    RELATE_ERR_UNSUPPORTED = -9         /* valid request this build does not handle */
+} relate_status_t;
+
+typedef enum { RELATE_F64 = 0, RELATE_F32 = 1, RELATE_BF16 = 2 } relate_dtype_t;
+
+/* How one mode's MTTKRP resolves writes of many nonzeros to one output row
+ * (Sec. 4.1.3: reduction-based vs atomic synchronisation, chosen from the
+ * tensor's fiber statistics, Sec. 4.2.1).
+ *  ATOMIC     - runs of equal i_n are merged in registers, then added to the
+ *               output with global atomics.
+ *  SEGMENTED  - the same runs, merged per partition in a shared-memory window
+ *               spanning the partition's [lo_n, hi_n] rows, flushed once per
+ *               partition (atomics only where a window does not fit).
+ *  PRIVATIZED - the whole output (I_n x R) is privatised in shared memory per
+ *               thread block and flushed once per block.
+ *  AUTO       - chosen per mode from the encode-time statistics. */
+typedef enum {
+    RELATE_CONFLICT_AUTO = 0,
+    RELATE_CONFLICT_ATOMIC = 1,
+    RELATE_CONFLICT_SEGMENTED = 2,
+    RELATE_CONFLICT_PRIVATIZED = 3
+} relate_conflict_t;
+
+typedef struct relate_handle_s *relate_handle_t; /* opaque; owns all encoding memory */
+
+typedef struct {
+    /* Bit order of the linear position p (Sec. 3.3.1-3.3.2): entry t names
+     * the mode whose next unused low bit becomes bit b^t of p. Host memory,
+     * bit_order_len = l(p) entries, each mode n exactly l(n) times (Alg. 1
+     * masking rule). NULL = the ALTO default order (Sec. 3.3, Fig. 4):
+     * round robin from b^0 over the modes sorted by (l(n), mode id),
+     * skipping exhausted modes. */
+    const int8_t *bit_order;
+    int bit_order_len;
+    /* Nonzeros per equal-work partition of the sorted stream; 0 = 4096. */
+    int64_t partition_size;
+    /* Per-mode conflict strategy; AUTO = chosen from the statistics. */
+    relate_conflict_t conflict[RELATE_MAX_MODES];
+    /* dtype of the vals array given to relate_encode: RELATE_F64 or F32.
+     * The handle keeps the values in this dtype. */
+    relate_dtype_t val_dtype;
+    /* Storage dtype of factor matrices given to relate_mttkrp/relate_cpals
+     * (F64, F32 or BF16) and accumulation dtype of the MTTKRP output
+     * (F64 for F64 factors; F32 for F32 and BF16 factors). */
+    relate_dtype_t factor_dtype;
+    relate_dtype_t acc_dtype;
+    /* 1: coords and vals are device pointers; 0: host pointers (the library
+     * copies them to the device inside relate_encode). */
+    int coords_on_device;
+    /* cudaStream_t used by relate_encode and relate_cpals. */
+    void *stream;
+    /* Shared-memory budget (bytes) per thread block for privatised
+     * accumulators; 0 = the device maximum minus what the kernel needs. */
+    int smem_budget;
+} relate_params_t;
+
+/* Fills *p with the defaults (ALTO order, S = 4096, AUTO conflicts, F32
+ * values, F32 factors, F32 accumulation, host inputs, default stream). */
+void relate_params_default(relate_params_t *p);
+
+/* Builds the linearized encoding on the device (Sec. 3.3):
+ *   1. l(n) = ceil(log2 I_n) (0 bits for I_n = 1), l(p) = sum l(n);
+ *   2. p = the coordinates' bits interleaved in bit_order (device kernel);
+ *   3. a stable radix sort of (p, original index) on the device;
+ *   4. the sorted stream is stored as one word of l(p) bits per nonzero --
+ *      the coordinates as concatenated bit fields, a fixed bit permutation of
+ *      p, so decoding is one shift and mask per mode -- plus the values;
+ *   5. equal-work partitions of partition_size nonzeros with per-partition
+ *      [lo_n, hi_n] bounds, and per-mode fiber statistics.
+ * coords: N x nnz uint32 SoA (host or device per params). vals: nnz values in
+ * params->val_dtype. dims: host, nmodes entries, each in [1, 2^32].
+ * nmodes in [2, 8]; nnz in [0, 2^32 - 1]. Inputs are not retained.
+ * Synchronises params->stream once (statistics to the host).
+ * Errors: INVALID_ARG, BAD_BIT_ORDER, KEY_TOO_WIDE, COORD_OUT_OF_RANGE, OOM,
+ * CUDA. On error *out is NULL and nothing is leaked. */
+int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims, int nmodes,
+                  int64_t nnz, const relate_params_t *params, relate_handle_t *out);
+
+/* Mode-n MTTKRP (Sec. 2.2, Fig. 2): for every nonzero (i_0..i_{N-1}, v),
+ *   out(i_n, :) += v * Hadamard_{k != n} A_k(i_k, :).
+ * factors: host array of nmodes DEVICE pointers, factors[k] is I_k x R in
+ * the handle's factor dtype; factors[mode] is not read (may be NULL).
+ * out: DEVICE, I_mode x R in the handle's acc dtype, overwritten (zeroed
+ * by this call). R in [1, 64]. Asynchronous on `stream`; never synchronises.
+ * Factor rows are read with 16-byte vector loads when every factor pointer
+ * is 16-byte aligned and R * sizeof(factor) is a multiple of 16; otherwise
+ * a scalar path runs. Errors: INVALID_ARG, CUDA (launch failure). */
+int relate_mttkrp(relate_handle_t h, int mode, void *const *factors, int R, void *out,
+                  void *stream);
+
+typedef struct {
+    double fit;          /* final fit 1 - ||X - Xhat|| / ||X|| */
+    int iters;           /* iterations run */
+    int status;          /* RELATE_OK or the failure status */
+    int ridge_retries;   /* Cholesky ridge retries taken */
+    double *fit_trace;   /* host, nullable: receives the fit of each iteration
+                            (must hold `iters` doubles as passed in) */
+} relate_cpals_info_t;
+
+/* CP-ALS (standard ALS, Gauss-Seidel over modes 0..N-1): per mode n,
+ *   M = MTTKRP_n; V = Hadamard_{k != n} A_k^T A_k (FP64); Cholesky of V in
+ *   FP64 (one ridge retry with 1e-12 tr(V)/R on the diagonal); A_n = M V^{-1};
+ *   lambda_r = ||A_n(:, r)||_2; columns scaled by 1/lambda_r (if > 0).
+ * After the last mode the fit is
+ *   1 - sqrt(max(0, ||X||^2 + lambda^T (Hadamard_k G_k) lambda
+ *                 - 2 sum_r lambda_r <M(:,r), A_{N-1}(:,r)>)) / ||X||
+ * and the loop stops when it > 1 and |fit - fit_prev| < tol, or after iters.
+ * factors: host array of nmodes DEVICE pointers (handle's factor dtype),
+ * in = initial factors, out = normalised factors. lambda: HOST, R doubles,
+ * out. info: nullable. Runs on the handle's stream; synchronises once per
+ * iteration (the fit). Errors: INVALID_ARG, NOT_PD, OOM, CUDA. */
+int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *factors,
+                 double *lambda, relate_cpals_info_t *info);
+
+typedef struct {
+    int nmodes;
+    int lp;                 /* l(p) */
+    int key_bytes;          /* 4, 8 or 16 bytes per stored word */
+    int64_t nnz;
+    int64_t partition_size;
+    int64_t partitions;
+    uint64_t dims[RELATE_MAX_MODES];
+    int lbits[RELATE_MAX_MODES];
+    int field_offset[RELATE_MAX_MODES]; /* bit offset of mode n's field in a word */
+    uint64_t runs[RELATE_MAX_MODES];     /* maximal runs of equal i_n within partitions */
+    uint64_t distinct[RELATE_MAX_MODES]; /* distinct values of i_n */
+    uint64_t maxcount[RELATE_MAX_MODES]; /* largest fiber-slice population */
+    int8_t bit_order[RELATE_MAX_KEY_BITS];
+} relate_stats_t;
+
+/* Encoding statistics (host struct filled from the handle). */
+int relate_get_stats(relate_handle_t h, relate_stats_t *s);
+
+/* Conflict strategy relate_mttkrp uses for `mode` at rank R (the AUTO rule
+ * or the explicit choice in params). */
+int relate_get_conflict(relate_handle_t h, int mode, int R, relate_conflict_t *out);
+
+/* Overrides the per-mode strategy (AUTO restores the rule). */
+int relate_set_conflict(relate_handle_t h, int mode, relate_conflict_t c);
+
+/* Changes the factor / accumulation dtypes used by later calls
+ * (F64/F64, F32/F32 or BF16/F32). */
+int relate_set_precision(relate_handle_t h, relate_dtype_t factor_dtype, relate_dtype_t acc_dtype);
+
+/* Changes the stream used by relate_cpals. */
+int relate_set_stream(relate_handle_t h, void *stream);
+
+/* Copies the encoded stream out, in encoded (sorted) order, to DEVICE
+ * buffers: coords_out N x nnz uint32 SoA (nullable), vals_out nnz values in
+ * the val dtype (nullable), perm_out nnz uint32 original indices (nullable),
+ * keys_out nnz x 2 uint64 (lo, hi) positions p (nullable). Async on stream. */
+int relate_decode(relate_handle_t h, uint32_t *coords_out, void *vals_out, uint32_t *perm_out,
+                  uint64_t *keys_out, void *stream);
+
+/* Copies the partition bounds to DEVICE buffers lo/hi, partitions x N
+ * uint32 each (row q, column n). Async on stream. */
+int relate_get_partitions(relate_handle_t h, uint32_t *lo, uint32_t *hi, void *stream);
+
+/* G = A^T A (the Gram step of CP-ALS) for a DEVICE matrix A (I x R,
+ * row-major, dtype F64/F32/BF16), written to DEVICE G (R x R FP64).
+ * FP64 inputs accumulate in FP64; FP32 and BF16 inputs accumulate in FP32
+ * within blocks of rows and in FP64 across blocks. Async on stream. */
+int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream);
+
+/* Frees the handle and all its device memory (synchronises its stream). */
+void relate_free(relate_handle_t h);
+
+/* Static description of a status code. */
+const char *relate_status_string(int status);
+
+/* Message of the last error on this host thread ("" if none). */
+const char *relate_last_error(void);
+
+/* Library version string. */
+const char *relate_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RELATE_H */

@@ -1,0 +1,671 @@
+// capi.cu -- the C ABI declared in include/relate.h: argument validation,
+// the device-memory lifetime of an encoding, the encode pipeline, MTTKRP
+// dispatch and the CP-ALS driver loop.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace relate;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int status, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(e == cudaErrorMemoryAllocation ? RELATE_ERR_OOM : RELATE_ERR_CUDA, "%s: %s (%s)", where,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+bool valid_precision(int f, int a) {
+    return (f == RELATE_F64 && a == RELATE_F64) || (f == RELATE_F32 && a == RELATE_F32) ||
+           (f == RELATE_BF16 && a == RELATE_F32);
+}
+
+int dtype_bytes(int d) { return d == RELATE_F64 ? 8 : d == RELATE_F32 ? 4 : 2; }
+
+}  // namespace
+
+struct relate_handle_s {
+    int N = 0;
+    int64_t nnz = 0;
+    uint64_t dims[kMaxModes] = {};
+    int lbits[kMaxModes] = {};
+    int lp = 0;
+    int KW = 1;
+    int8_t order[RELATE_MAX_KEY_BITS] = {};
+    BitRuns runs{};
+    Fields fields{};
+    int64_t S = 4096, P = 0;
+    relate_dtype_t val_dtype = RELATE_F32, factor_dtype = RELATE_F32, acc_dtype = RELATE_F32;
+    relate_conflict_t conflict[kMaxModes] = {};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 152, smem_optin = 0, smem_budget = 0;
+
+    void *d_words = nullptr;
+    void *d_vals = nullptr;
+    uint32_t *d_perm = nullptr;
+    uint32_t *d_plo = nullptr, *d_phi = nullptr;
+    uint32_t *d_counts[kMaxModes] = {};
+    double *d_normX2 = nullptr;
+    uint64_t runs_n[kMaxModes] = {}, distinct[kMaxModes] = {}, maxcount[kMaxModes] = {};
+
+    // CP-ALS workspace (grown on demand)
+    int ws_R = 0;
+    void *d_M = nullptr;
+    double *d_scratch = nullptr, *d_G = nullptr, *d_Vinv = nullptr, *d_lambda = nullptr, *d_inner = nullptr,
+           *d_fit = nullptr;
+    float *d_Vinv32 = nullptr;
+    int *d_status = nullptr;
+
+    ~relate_handle_s() {
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
+        void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_M, d_scratch, d_G, d_Vinv,
+                        d_lambda, d_inner, d_fit, d_Vinv32, d_status};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        for (auto *p : d_counts)
+            if (p) cudaFree(p);
+    }
+};
+
+namespace {
+
+relate_conflict_t resolve_conflict(const relate_handle_s *h, int mode, int R) {
+    if (h->conflict[mode] != RELATE_CONFLICT_AUTO) return h->conflict[mode];
+    const int accb = mttkrp_acc_bytes(h->factor_dtype);
+    const uint64_t priv_bytes = h->dims[mode] * (uint64_t)R * accb;
+    // whole-output privatisation when it leaves room for >= 2 blocks per SM
+    if (priv_bytes <= 96u * 1024u && priv_bytes <= (uint64_t)h->smem_budget) return RELATE_CONFLICT_PRIVATIZED;
+    const double reuse = h->distinct[mode] ? (double)h->nnz / (double)h->distinct[mode] : 0.0;
+    const double mean_run = h->runs_n[mode] ? (double)h->nnz / (double)h->runs_n[mode] : 0.0;
+    // "minimum fiber reuse 8" (Sec. 4.1.3) for reduction-based synchronisation
+    if (reuse >= 8.0 || mean_run >= 8.0) return RELATE_CONFLICT_SEGMENTED;
+    return RELATE_CONFLICT_ATOMIC;
+}
+
+int build_runs(relate_handle_s *h) {
+    struct Run {
+        int mode, src, dst, len;
+    };
+    std::vector<Run> runs;
+    int next[kMaxModes] = {};
+    for (int t = 0; t < h->lp; t++) {
+        const int m = h->order[t];
+        const int s = next[m]++;
+        if (!runs.empty() && runs.back().mode == m && runs.back().dst + runs.back().len == t &&
+            runs.back().src + runs.back().len == s)
+            runs.back().len++;
+        else
+            runs.push_back({m, s, t, 1});
+    }
+    BitRuns br{};
+    int off = 0;
+    for (int m = 0; m < kMaxModes; m++) {
+        br.mode_begin[m] = br.nruns;
+        br.field_off[m] = m < h->N ? off : 0;
+        if (m < h->N) {
+            for (const Run &r : runs)
+                if (r.mode == m) {
+                    br.src[br.nruns] = (uint8_t)r.src;
+                    br.dst[br.nruns] = (uint8_t)r.dst;
+                    br.len[br.nruns] = (uint8_t)r.len;
+                    br.nruns++;
+                }
+            off += h->lbits[m];
+        }
+    }
+    br.mode_begin[kMaxModes] = br.nruns;
+    h->runs = br;
+    for (int m = 0; m < kMaxModes; m++) {
+        h->fields.shift[m] = br.field_off[m];
+        const int l = m < h->N ? h->lbits[m] : 0;
+        h->fields.mask[m] = l >= 32 ? 0xffffffffu : ((1u << l) - 1u);
+    }
+    return RELATE_OK;
+}
+
+int bits_for(uint64_t I) {
+    int b = 0;
+    while (b < 64 && ((uint64_t)1 << b) < I) b++;
+    return b;
+}
+
+struct AsyncBufs {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    cudaError_t alloc(void **p, size_t bytes) {
+        *p = nullptr;
+        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    ~AsyncBufs() {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+int ensure_ws(relate_handle_s *h, int R) {
+    if (h->ws_R >= R && h->d_M) return RELATE_OK;
+    void *ptrs[] = {h->d_M, h->d_scratch, h->d_G, h->d_Vinv, h->d_lambda, h->d_inner, h->d_fit, h->d_Vinv32,
+                    h->d_status};
+    cudaStreamSynchronize(h->stream);
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    h->d_M = nullptr;
+    h->d_scratch = h->d_G = h->d_Vinv = h->d_lambda = h->d_inner = h->d_fit = nullptr;
+    h->d_Vinv32 = nullptr;
+    h->d_status = nullptr;
+    h->ws_R = 0;
+    uint64_t maxI = 0;
+    for (int m = 0; m < h->N; m++) maxI = h->dims[m] > maxI ? h->dims[m] : maxI;
+    const int RM = RELATE_MAX_RANK;
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->d_M, maxI * RM * 8 + 16)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_scratch, dense_scratch_doubles(RM) * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_G, (size_t)h->N * RM * RM * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_Vinv, RM * RM * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_Vinv32, RM * RM * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_lambda, RM * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_inner, RM * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_fit, 64)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_status, 64)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals workspace");
+    h->ws_R = RM;
+    return RELATE_OK;
+}
+
+int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *out, cudaStream_t st) {
+    MttkrpArgs a{};
+    a.words = h->d_words;
+    a.vals = h->d_vals;
+    a.nnz = h->nnz;
+    a.S = h->S;
+    a.P = h->P;
+    a.N = h->N;
+    a.mode = mode;
+    a.fields = h->fields;
+    for (int k = 0; k < h->N; k++) a.factors[k] = factors[k];
+    a.R = R;
+    a.out = out;
+    a.In = h->dims[mode];
+    a.plo = h->d_plo;
+    a.phi = h->d_phi;
+    a.strategy = resolve_conflict(h, mode, R);
+    const int accb = mttkrp_acc_bytes(h->factor_dtype);
+    if (a.strategy == RELATE_CONFLICT_PRIVATIZED && h->dims[mode] * (uint64_t)R * accb > (uint64_t)h->smem_budget)
+        a.strategy = RELATE_CONFLICT_SEGMENTED;  // explicit request that does not fit
+    cudaError_t e = cudaMemsetAsync(out, 0, h->dims[mode] * (size_t)R * accb, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp memset");
+    e = launch_mttkrp(a, h->KW, h->factor_dtype, h->val_dtype, h->smem_budget, h->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp launch");
+    return RELATE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void relate_params_default(relate_params_t *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->bit_order = nullptr;
+    p->bit_order_len = 0;
+    p->partition_size = 0;
+    for (int m = 0; m < RELATE_MAX_MODES; m++) p->conflict[m] = RELATE_CONFLICT_AUTO;
+    p->val_dtype = RELATE_F32;
+    p->factor_dtype = RELATE_F32;
+    p->acc_dtype = RELATE_F32;
+    p->coords_on_device = 0;
+    p->stream = nullptr;
+    p->smem_budget = 0;
+}
+
+int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims, int nmodes, int64_t nnz,
+                  const relate_params_t *params, relate_handle_t *out) {
+    g_err[0] = 0;
+    if (!out) return fail(RELATE_ERR_INVALID_ARG, "relate_encode: out is NULL");
+    *out = nullptr;
+    relate_params_t defaults;
+    relate_params_default(&defaults);
+    const relate_params_t *p = params ? params : &defaults;
+    if (nmodes < 2 || nmodes > RELATE_MAX_MODES)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_encode: nmodes=%d not in [2, %d]", nmodes, RELATE_MAX_MODES);
+    if (!dims) return fail(RELATE_ERR_INVALID_ARG, "relate_encode: dims is NULL");
+    if (nnz < 0 || nnz > (int64_t)0xffffffffLL)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_encode: nnz=%lld out of range", (long long)nnz);
+    if (nnz > 0 && (!coords || !vals)) return fail(RELATE_ERR_INVALID_ARG, "relate_encode: coords/vals NULL");
+    if (p->val_dtype != RELATE_F64 && p->val_dtype != RELATE_F32)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_encode: val_dtype must be F64 or F32");
+    if (!valid_precision(p->factor_dtype, p->acc_dtype))
+        return fail(RELATE_ERR_INVALID_ARG, "relate_encode: factor/acc dtype pair not supported");
+    if (p->partition_size < 0) return fail(RELATE_ERR_INVALID_ARG, "relate_encode: partition_size < 0");
+    for (int m = 0; m < nmodes; m++)
+        if (p->conflict[m] < RELATE_CONFLICT_AUTO || p->conflict[m] > RELATE_CONFLICT_PRIVATIZED)
+            return fail(RELATE_ERR_INVALID_ARG, "relate_encode: bad conflict strategy for mode %d", m);
+
+    relate_handle_s *h = new (std::nothrow) relate_handle_s();
+    if (!h) return fail(RELATE_ERR_OOM, "relate_encode: host allocation");
+    h->N = nmodes;
+    h->nnz = nnz;
+    h->lp = 0;
+    for (int m = 0; m < nmodes; m++) {
+        if (dims[m] < 1 || dims[m] > ((uint64_t)1 << 32)) {
+            delete h;
+            return fail(RELATE_ERR_INVALID_ARG, "relate_encode: dims[%d]=%llu not in [1, 2^32]", m,
+                        (unsigned long long)dims[m]);
+        }
+        h->dims[m] = dims[m];
+        h->lbits[m] = bits_for(dims[m]);
+        h->lp += h->lbits[m];
+    }
+    if (h->lp > RELATE_MAX_KEY_BITS) {
+        delete h;
+        return fail(RELATE_ERR_KEY_TOO_WIDE, "relate_encode: l(p)=%d > 128", h->lp);
+    }
+    // bit order: explicit (validated by the masking rule) or ALTO default
+    if (p->bit_order) {
+        if (p->bit_order_len != h->lp) {
+            delete h;
+            return fail(RELATE_ERR_BAD_BIT_ORDER, "relate_encode: bit order length %d != l(p) %d", p->bit_order_len,
+                        h->lp);
+        }
+        int used[kMaxModes] = {};
+        for (int t = 0; t < h->lp; t++) {
+            const int m = p->bit_order[t];
+            if (m < 0 || m >= nmodes) {
+                delete h;
+                return fail(RELATE_ERR_BAD_BIT_ORDER, "relate_encode: bit order entry %d names mode %d", t, m);
+            }
+            used[m]++;
+            h->order[t] = (int8_t)m;
+        }
+        for (int m = 0; m < nmodes; m++)
+            if (used[m] != h->lbits[m]) {
+                delete h;
+                return fail(RELATE_ERR_BAD_BIT_ORDER, "relate_encode: mode %d appears %d times, needs l(n)=%d", m,
+                            used[m], h->lbits[m]);
+            }
+    } else {
+        int rank[kMaxModes], left[kMaxModes];
+        for (int m = 0; m < nmodes; m++) rank[m] = m;
+        for (int a = 0; a < nmodes; a++)  // stable order by (l(n), id)
+            for (int b = a + 1; b < nmodes; b++)
+                if (h->lbits[rank[b]] < h->lbits[rank[a]]) {
+                    int t = rank[a];
+                    rank[a] = rank[b];
+                    rank[b] = t;
+                } else if (h->lbits[rank[b]] == h->lbits[rank[a]] && rank[b] < rank[a]) {
+                    int t = rank[a];
+                    rank[a] = rank[b];
+                    rank[b] = t;
+                }
+        for (int m = 0; m < nmodes; m++) left[m] = h->lbits[m];
+        int t = 0;
+        while (t < h->lp)
+            for (int a = 0; a < nmodes; a++)
+                if (left[rank[a]] > 0) {
+                    h->order[t++] = (int8_t)rank[a];
+                    left[rank[a]]--;
+                }
+    }
+    h->KW = h->lp <= 32 ? 1 : h->lp <= 64 ? 2 : 4;
+    build_runs(h);
+    h->S = p->partition_size > 0 ? p->partition_size : 4096;
+    h->P = (nnz + h->S - 1) / h->S;
+    h->val_dtype = p->val_dtype;
+    h->factor_dtype = p->factor_dtype;
+    h->acc_dtype = p->acc_dtype;
+    for (int m = 0; m < kMaxModes; m++) h->conflict[m] = m < nmodes ? p->conflict[m] : RELATE_CONFLICT_AUTO;
+    h->stream = (cudaStream_t)p->stream;
+
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device)) !=
+            cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "relate_encode: device query");
+    }
+    h->smem_budget = h->smem_optin - 2048;
+    if (p->smem_budget > 0 && p->smem_budget < h->smem_budget) h->smem_budget = p->smem_budget;
+
+    const cudaStream_t st = h->stream;
+    const int vb = h->val_dtype == RELATE_F64 ? 8 : 4;
+    const size_t kb = 4u * h->KW;
+    const int N = nmodes;
+    int rc = RELATE_OK;
+    {
+        AsyncBufs tmp{st, {}};
+        void *d_coords = nullptr, *d_vin = nullptr, *keys = nullptr, *keys_alt = nullptr, *idx = nullptr,
+             *idx_alt = nullptr, *sort_tmp = nullptr, *d_dims = nullptr, *d_small = nullptr;
+        const size_t sort_bytes = radix_sort_temp_bytes(nnz);
+        // persistent encoding arrays
+        if ((e = cudaMalloc(&h->d_words, nnz * kb + 16)) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_vals, nnz * vb + 16)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&h->d_plo, (h->P + 1) * N * 4)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&h->d_phi, (h->P + 1) * N * 4)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&h->d_normX2, 64)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: allocation");
+            goto done;
+        }
+        for (int m = 0; m < N; m++)
+            if ((e = cudaMalloc((void **)&h->d_counts[m], h->dims[m] * 4)) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: allocation");
+                goto done;
+            }
+        if ((e = tmp.alloc(&keys, nnz * kb)) != cudaSuccess || (e = tmp.alloc(&keys_alt, nnz * kb)) != cudaSuccess ||
+            (e = tmp.alloc(&idx, nnz * 4)) != cudaSuccess || (e = tmp.alloc(&idx_alt, nnz * 4)) != cudaSuccess ||
+            (e = tmp.alloc(&sort_tmp, sort_bytes)) != cudaSuccess || (e = tmp.alloc(&d_dims, 64)) != cudaSuccess ||
+            (e = tmp.alloc(&d_small, 8 * (1 + 3 * kMaxModes) + 1024 * 8)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: temporary allocation");
+            goto done;
+        }
+        const uint32_t *c_dev = coords;
+        const void *v_dev = vals;
+        if (!p->coords_on_device && nnz > 0) {
+            if ((e = tmp.alloc(&d_coords, (size_t)N * nnz * 4)) != cudaSuccess ||
+                (e = tmp.alloc(&d_vin, (size_t)nnz * vb)) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: input staging");
+                goto done;
+            }
+            if ((e = cudaMemcpyAsync(d_coords, coords, (size_t)N * nnz * 4, cudaMemcpyHostToDevice, st)) !=
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(d_vin, vals, (size_t)nnz * vb, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: host-to-device copy");
+                goto done;
+            }
+            c_dev = (const uint32_t *)d_coords;
+            v_dev = d_vin;
+        }
+        // d_small layout: [0] err flag (u32 in a u64 slot) | runs[8] | summary[2*8] | sumsq partials
+        uint32_t *d_err = (uint32_t *)d_small;
+        unsigned long long *d_runs = (unsigned long long *)d_small + 1;
+        unsigned long long *d_summ = d_runs + kMaxModes;
+        double *d_part = (double *)(d_summ + 2 * kMaxModes);
+        if ((e = cudaMemsetAsync(d_small, 0, 8 * (1 + 3 * kMaxModes), st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d_dims, h->dims, sizeof(uint64_t) * N, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: setup");
+            goto done;
+        }
+        for (int m = 0; m < N; m++)
+            if ((e = cudaMemsetAsync(h->d_counts[m], 0, h->dims[m] * 4, st)) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: setup");
+                goto done;
+            }
+        bool in_alt = false;
+        if ((e = launch_build_keys(h->KW, c_dev, (const uint64_t *)d_dims, nnz, N, h->runs, keys, (uint32_t *)idx,
+                                   d_err, st)) != cudaSuccess ||
+            (e = radix_sort_pairs(h->KW, keys, (uint32_t *)idx, keys_alt, (uint32_t *)idx_alt, nnz, h->lp, sort_tmp,
+                                  sort_bytes, st, &in_alt)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: key build / sort");
+            goto done;
+        }
+        void *skeys = in_alt ? keys_alt : keys;
+        uint32_t *sperm = (uint32_t *)(in_alt ? idx_alt : idx);
+        if ((e = cudaMalloc((void **)&h->d_perm, nnz * 4 + 16)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h->d_perm, sperm, nnz * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = launch_make_words(h->KW, skeys, nnz, h->runs, h->d_words, st)) != cudaSuccess ||
+            (e = launch_gather(v_dev, sperm, nnz, vb, h->d_vals, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: words / gather");
+            goto done;
+        }
+        CountPtrs cp{};
+        for (int m = 0; m < N; m++) {
+            cp.p[m] = h->d_counts[m];
+            cp.len[m] = h->dims[m];
+        }
+        if ((e = launch_partition_stats(h->KW, h->d_words, nnz, N, h->fields, h->S, h->d_plo, h->d_phi, d_runs, cp,
+                                        st)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: partition statistics");
+            goto done;
+        }
+        for (int m = 0; m < N; m++)
+            if ((e = launch_hist_summary(h->d_counts[m], h->dims[m], d_summ + 2 * m, st)) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: histogram summary");
+                goto done;
+            }
+        if ((e = launch_sum_squares(h->d_vals, nnz, vb, d_part, h->d_normX2, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: norm");
+            goto done;
+        }
+        unsigned long long host_small[1 + 3 * kMaxModes];
+        if ((e = cudaMemcpyAsync(host_small, d_small, sizeof(host_small), cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: statistics to host");
+            goto done;
+        }
+        if ((uint32_t)host_small[0] != 0) {
+            rc = fail(RELATE_ERR_COORD_OUT_OF_RANGE, "relate_encode: a coordinate is >= its mode length");
+            goto done;
+        }
+        for (int m = 0; m < N; m++) {
+            h->runs_n[m] = host_small[1 + m];
+            h->distinct[m] = host_small[1 + kMaxModes + 2 * m];
+            h->maxcount[m] = host_small[1 + kMaxModes + 2 * m + 1];
+        }
+    }
+done:
+    if (rc != RELATE_OK) {
+        delete h;
+        return rc;
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "relate_encode: release temporaries");
+    }
+    *out = h;
+    return RELATE_OK;
+}
+
+int relate_mttkrp(relate_handle_t h, int mode, void *const *factors, int R, void *out, void *stream) {
+    g_err[0] = 0;
+    if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp: NULL handle");
+    if (mode < 0 || mode >= h->N) return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp: mode %d out of range", mode);
+    if (R < 1 || R > RELATE_MAX_RANK) return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp: R=%d not in [1, 64]", R);
+    if (!factors || !out) return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp: NULL factors/out");
+    for (int k = 0; k < h->N; k++)
+        if (k != mode && !factors[k]) return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp: factors[%d] is NULL", k);
+    return run_mttkrp(h, mode, factors, R, out, (cudaStream_t)stream);
+}
+
+int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *factors, double *lambda,
+                 relate_cpals_info_t *info) {
+    g_err[0] = 0;
+    if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals: NULL handle");
+    if (R < 1 || R > RELATE_MAX_RANK) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals: R=%d not in [1, 64]", R);
+    if (iters < 0 || !factors || !lambda) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals: bad iters/factors/lambda");
+    for (int k = 0; k < h->N; k++)
+        if (!factors[k]) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals: factors[%d] is NULL", k);
+    int rc = ensure_ws(h, R);
+    if (rc) return rc;
+    const cudaStream_t st = h->stream;
+    const int N = h->N;
+    const int RR = R * R;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->d_status, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "relate_cpals: setup");
+    for (int k = 0; k < N; k++)
+        if ((e = launch_gram(factors[k], (int64_t)h->dims[k], R, h->factor_dtype, h->d_scratch, h->d_G + k * RR, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "relate_cpals: initial Gram");
+    double prev = 0.0, fit = 0.0;
+    int done = 0;
+    int hstatus[2] = {0, 0};
+    for (int it = 1; it <= iters; it++) {
+        for (int n = 0; n < N; n++) {
+            const int64_t In = (int64_t)h->dims[n];
+            rc = run_mttkrp(h, n, factors, R, h->d_M, st);
+            if (rc) return rc;
+            if ((e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_status, st)) != cudaSuccess ||
+                (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_scratch, st)) !=
+                    cudaSuccess ||
+                (e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) != cudaSuccess ||
+                (e = launch_finish_mode(h->d_scratch, In, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) !=
+                    cudaSuccess ||
+                (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype, st)) !=
+                    cudaSuccess)
+                return cuda_fail(e, "relate_cpals: mode update");
+        }
+        if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: fit");
+        if ((e = cudaMemcpyAsync(&fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hstatus, h->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: fit to host");
+        done = it;
+        if (info && info->fit_trace) info->fit_trace[it - 1] = fit;
+        if (hstatus[1]) break;
+        if (it > 1 && (fit - prev < tol && prev - fit < tol)) break;
+        prev = fit;
+    }
+    if ((e = cudaMemcpyAsync(lambda, h->d_lambda, sizeof(double) * R, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals: lambda to host");
+    rc = hstatus[1] ? fail(RELATE_ERR_NOT_PD, "relate_cpals: normal equations not positive definite") : RELATE_OK;
+    if (info) {
+        info->fit = fit;
+        info->iters = done;
+        info->status = rc;
+        info->ridge_retries = hstatus[0];
+    }
+    return rc;
+}
+
+int relate_get_stats(relate_handle_t h, relate_stats_t *s) {
+    g_err[0] = 0;
+    if (!h || !s) return fail(RELATE_ERR_INVALID_ARG, "relate_get_stats: NULL argument");
+    memset(s, 0, sizeof(*s));
+    s->nmodes = h->N;
+    s->lp = h->lp;
+    s->key_bytes = 4 * h->KW;
+    s->nnz = h->nnz;
+    s->partition_size = h->S;
+    s->partitions = h->P;
+    for (int m = 0; m < h->N; m++) {
+        s->dims[m] = h->dims[m];
+        s->lbits[m] = h->lbits[m];
+        s->field_offset[m] = h->runs.field_off[m];
+        s->runs[m] = h->runs_n[m];
+        s->distinct[m] = h->distinct[m];
+        s->maxcount[m] = h->maxcount[m];
+    }
+    memcpy(s->bit_order, h->order, RELATE_MAX_KEY_BITS);
+    return RELATE_OK;
+}
+
+int relate_get_conflict(relate_handle_t h, int mode, int R, relate_conflict_t *out) {
+    g_err[0] = 0;
+    if (!h || !out || mode < 0 || mode >= h->N || R < 1 || R > RELATE_MAX_RANK)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_get_conflict: bad argument");
+    *out = resolve_conflict(h, mode, R);
+    return RELATE_OK;
+}
+
+int relate_set_conflict(relate_handle_t h, int mode, relate_conflict_t c) {
+    g_err[0] = 0;
+    if (!h || mode < 0 || mode >= h->N || c < RELATE_CONFLICT_AUTO || c > RELATE_CONFLICT_PRIVATIZED)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_set_conflict: bad argument");
+    h->conflict[mode] = c;
+    return RELATE_OK;
+}
+
+int relate_set_precision(relate_handle_t h, relate_dtype_t factor_dtype, relate_dtype_t acc_dtype) {
+    g_err[0] = 0;
+    if (!h || !valid_precision(factor_dtype, acc_dtype))
+        return fail(RELATE_ERR_INVALID_ARG, "relate_set_precision: unsupported dtype pair");
+    h->factor_dtype = factor_dtype;
+    h->acc_dtype = acc_dtype;
+    return RELATE_OK;
+}
+
+int relate_set_stream(relate_handle_t h, void *stream) {
+    g_err[0] = 0;
+    if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_set_stream: NULL handle");
+    h->stream = (cudaStream_t)stream;
+    return RELATE_OK;
+}
+
+int relate_decode(relate_handle_t h, uint32_t *coords_out, void *vals_out, uint32_t *perm_out, uint64_t *keys_out,
+                  void *stream) {
+    g_err[0] = 0;
+    if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_decode: NULL handle");
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int vb = h->val_dtype == RELATE_F64 ? 8 : 4;
+    cudaError_t e = cudaSuccess;
+    if (coords_out && (e = launch_decode_words(h->KW, h->d_words, h->nnz, h->N, h->fields, coords_out, st)))
+        return cuda_fail(e, "relate_decode: coordinates");
+    if (vals_out && h->nnz &&
+        (e = cudaMemcpyAsync(vals_out, h->d_vals, (size_t)h->nnz * vb, cudaMemcpyDeviceToDevice, st)))
+        return cuda_fail(e, "relate_decode: values");
+    if (perm_out && h->nnz &&
+        (e = cudaMemcpyAsync(perm_out, h->d_perm, (size_t)h->nnz * 4, cudaMemcpyDeviceToDevice, st)))
+        return cuda_fail(e, "relate_decode: permutation");
+    if (keys_out && (e = launch_words_to_keys(h->KW, h->d_words, h->nnz, h->runs, keys_out, st)))
+        return cuda_fail(e, "relate_decode: positions");
+    return RELATE_OK;
+}
+
+int relate_get_partitions(relate_handle_t h, uint32_t *lo, uint32_t *hi, void *stream) {
+    g_err[0] = 0;
+    if (!h || !lo || !hi) return fail(RELATE_ERR_INVALID_ARG, "relate_get_partitions: NULL argument");
+    const size_t bytes = (size_t)h->P * h->N * 4;
+    if (!bytes) return RELATE_OK;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(lo, h->d_plo, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream)) ||
+        (e = cudaMemcpyAsync(hi, h->d_phi, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream)))
+        return cuda_fail(e, "relate_get_partitions");
+    return RELATE_OK;
+}
+
+int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream) {
+    g_err[0] = 0;
+    if ((!A && I > 0) || !G || I < 0 || R < 1 || R > RELATE_MAX_RANK ||
+        (dtype != RELATE_F64 && dtype != RELATE_F32 && dtype != RELATE_BF16))
+        return fail(RELATE_ERR_INVALID_ARG, "relate_gram: bad argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, dense_scratch_doubles(R) * 8, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_gram: scratch");
+    e = launch_gram(A, I, R, dtype, (double *)scratch, G, st);
+    cudaError_t e2 = cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_gram: launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "relate_gram: free");
+    return RELATE_OK;
+}
+
+void relate_free(relate_handle_t h) { delete h; }
+
+const char *relate_status_string(int status) {
+    switch (status) {
+    case RELATE_OK: return "ok";
+    case RELATE_ERR_INVALID_ARG: return "invalid argument";
+    case RELATE_ERR_BAD_BIT_ORDER: return "bit order breaks the masking rule (mode n must appear l(n) times)";
+    case RELATE_ERR_KEY_TOO_WIDE: return "linear position wider than 128 bits";
+    case RELATE_ERR_COORD_OUT_OF_RANGE: return "coordinate out of range";
+    case RELATE_ERR_OOM: return "out of device memory";
+    case RELATE_ERR_NOT_PD: return "normal equations not positive definite";
+    case RELATE_ERR_TIMEOUT: return "bounded device wait timed out";
+    case RELATE_ERR_CUDA: return "CUDA error";
+    case RELATE_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+const char *relate_last_error(void) { return g_err; }
+
+const char *relate_version(void) { return RELATE_VERSION_STRING; }
+
+}  // extern "C"

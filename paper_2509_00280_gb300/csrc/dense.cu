@@ -1,0 +1,363 @@
+// dense.cu -- the dense remainder of CP-ALS around the MTTKRP.
+//
+// The paper accelerates CP decomposition (Sec. 2.2) and cites the standard
+// ALS of Kolda & Bader for it; per mode n the update is
+//   V = Hadamard_{k != n} (A_k^T A_k),  A_n = M V^{-1},
+//   lambda_r = ||A_n(:, r)||_2, columns normalised,
+// and after a sweep the fit uses ||X||^2 + lambda^T (Hadamard_k G_k) lambda
+// - 2 <M, A_{N-1} diag(lambda)>. The normal-equations factorisation, the
+// normalisation and the fit run in FP64 on the GPU (R <= 64, one block);
+// the tall-skinny Gram and the row passes stream the I x R matrices.
+#include "internal.cuh"
+
+namespace relate {
+namespace {
+
+constexpr int GR_ROWS = 32;    // rows per staged tile of the Gram kernel
+constexpr int GR_BLOCKS = 304; // 2 blocks per SM on 152 SMs
+constexpr int MAXR = RELATE_MAX_RANK;
+constexpr int MAXPAIRS = MAXR * (MAXR + 1) / 2;
+constexpr int PAIRS_PER_THREAD = (MAXPAIRS + kThreads - 1) / kThreads;
+
+template <typename FT> struct GramAcc { using T = float; };
+template <> struct GramAcc<double> { using T = double; };
+
+template <typename FT> __device__ __forceinline__ typename GramAcc<FT>::T ld_as(const FT *p) { return *p; }
+template <> __device__ __forceinline__ float ld_as<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(*p);
+}
+
+__device__ __forceinline__ void pair_of(int p, int R, int &r, int &s) {
+    int row = 0, left = p;
+    while (left >= R - row) {
+        left -= R - row;
+        row++;
+    }
+    r = row;
+    s = row + left;
+}
+
+// Per-block partial of the upper triangle of A^T A. FP32/BF16 inputs
+// accumulate in FP32 within a 32-row tile and in FP64 across tiles.
+template <typename FT>
+__global__ void __launch_bounds__(kThreads) k_gram_partial(const FT *__restrict__ A, int64_t I, int R,
+                                                           double *__restrict__ partial) {
+    using T = typename GramAcc<FT>::T;
+    __shared__ T tile[GR_ROWS][MAXR + 1];
+    const int npairs = R * (R + 1) / 2;
+    int pr[PAIRS_PER_THREAD], ps[PAIRS_PER_THREAD];
+    double acc[PAIRS_PER_THREAD];
+#pragma unroll
+    for (int u = 0; u < PAIRS_PER_THREAD; u++) {
+        const int p = threadIdx.x + u * kThreads;
+        pr[u] = ps[u] = 0;
+        if (p < npairs) pair_of(p, R, pr[u], ps[u]);
+        acc[u] = 0.0;
+    }
+    for (int64_t r0 = (int64_t)blockIdx.x * GR_ROWS; r0 < I; r0 += (int64_t)gridDim.x * GR_ROWS) {
+        for (int idx = threadIdx.x; idx < GR_ROWS * R; idx += kThreads) {
+            const int i = idx / R, c = idx - i * R;
+            const int64_t row = r0 + i;
+            tile[i][c] = row < I ? ld_as<FT>(A + row * R + c) : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PAIRS_PER_THREAD; u++) {
+            if (threadIdx.x + u * kThreads < npairs) {
+                T s = T(0);
+#pragma unroll 8
+                for (int i = 0; i < GR_ROWS; i++) s = fma(tile[i][pr[u]], tile[i][ps[u]], s);
+                acc[u] += (double)s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < PAIRS_PER_THREAD; u++) {
+        const int p = threadIdx.x + u * kThreads;
+        if (p < npairs) partial[(int64_t)blockIdx.x * npairs + p] = acc[u];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gram_reduce(const double *__restrict__ partial, int nblocks, int R,
+                                                          double *__restrict__ G) {
+    const int npairs = R * (R + 1) / 2;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; b++) s += partial[(int64_t)b * npairs + p];
+        int r, c;
+        pair_of(p, R, r, c);
+        G[r * R + c] = s;
+        G[c * R + r] = s;
+    }
+}
+
+// V = Hadamard_{k != n} G_k, Cholesky (FP64, one ridge retry), V^{-1}.
+__global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict__ G_all, int N, int n, int R,
+                                                        double *__restrict__ Vinv, float *__restrict__ Vinv32,
+                                                        int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double(*L)[MAXR + 1] = reinterpret_cast<double(*)[MAXR + 1]>(smem_raw);
+    double(*Li)[MAXR + 1] = reinterpret_cast<double(*)[MAXR + 1]>(smem_raw + sizeof(double) * MAXR * (MAXR + 1));
+    __shared__ int fail;
+    __shared__ double ridge;
+    const int RR = R * R;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
+            double v = 1.0;
+            for (int k = 0; k < N; k++)
+                if (k != n) v *= G_all[(int64_t)k * RR + idx];
+            L[idx / R][idx % R] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fail = 0;
+            if (attempt == 0) {
+                double tr = 0.0;
+                for (int r = 0; r < R; r++) tr += L[r][r];
+                ridge = 1e-12 * tr / R;
+            }
+        }
+        __syncthreads();
+        if (attempt == 1)
+            for (int r = threadIdx.x; r < R; r += kThreads) L[r][r] += ridge;
+        __syncthreads();
+        for (int j = 0; j < R; j++) {
+            if (threadIdx.x == 0) {
+                const double d = L[j][j];
+                if (!(d > 0.0))
+                    fail = 1;
+                else
+                    L[j][j] = sqrt(d);
+            }
+            __syncthreads();
+            if (fail) break;
+            for (int i = j + 1 + threadIdx.x; i < R; i += kThreads) L[i][j] /= L[j][j];
+            __syncthreads();
+            const int m = R - j - 1;
+            for (int t = threadIdx.x; t < m * m; t += kThreads) {
+                const int i = j + 1 + t / m, k = j + 1 + t % m;
+                if (k <= i) L[i][k] -= L[i][j] * L[k][j];
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!fail) break;
+        if (threadIdx.x == 0 && attempt == 0) status[0] += 1;
+        __syncthreads();
+    }
+    if (fail) {
+        if (threadIdx.x == 0) status[1] = 1;
+        for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
+            Vinv[idx] = 0.0;
+            Vinv32[idx] = 0.0f;
+        }
+        return;
+    }
+    // L^{-1} column by column (forward substitution on unit vectors)
+    for (int c = threadIdx.x; c < R; c += kThreads) {
+        for (int i = 0; i < c; i++) Li[i][c] = 0.0;
+        Li[c][c] = 1.0 / L[c][c];
+        for (int i = c + 1; i < R; i++) {
+            double s = 0.0;
+            for (int k = c; k < i; k++) s += L[i][k] * Li[k][c];
+            Li[i][c] = -s / L[i][i];
+        }
+    }
+    __syncthreads();
+    // V^{-1} = L^{-T} L^{-1}
+    for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
+        const int i = idx / R, j = idx % R;
+        double s = 0.0;
+        for (int k = max(i, j); k < R; k++) s += Li[k][i] * Li[k][j];
+        Vinv[idx] = s;
+        Vinv32[idx] = (float)s;
+    }
+}
+
+// In place M <- M V^{-1} (one warp per row, lane c owns columns c, c+32),
+// plus per-block partials of <M_old(:, c), M_new(:, c)>.
+template <typename C>
+__global__ void __launch_bounds__(kThreads) k_solve_rows(C *__restrict__ M, int64_t I, int R,
+                                                         const C *__restrict__ Vinv, double *__restrict__ partial) {
+    __shared__ C Vs[MAXR][MAXR];
+    __shared__ double red[kThreads / 32][MAXR];
+    for (int idx = threadIdx.x; idx < R * R; idx += kThreads) Vs[idx / R][idx % R] = Vinv[idx];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = lane, c1 = lane + 32;
+    double d0 = 0.0, d1 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + warp; i < I; i += (int64_t)gridDim.x * (kThreads / 32)) {
+        C *row = M + i * R;
+        const C x0 = c0 < R ? row[c0] : C(0);
+        const C x1 = c1 < R ? row[c1] : C(0);
+        C y0 = C(0), y1 = C(0);
+        for (int r = 0; r < R; r++) {
+            const C xr = __shfl_sync(0xffffffffu, r < 32 ? x0 : x1, r & 31);
+            if (c0 < R) y0 = fma(xr, Vs[r][c0], y0);
+            if (c1 < R) y1 = fma(xr, Vs[r][c1], y1);
+        }
+        if (c0 < R) {
+            row[c0] = y0;
+            d0 += (double)x0 * (double)y0;
+        }
+        if (c1 < R) {
+            row[c1] = y1;
+            d1 += (double)x1 * (double)y1;
+        }
+    }
+    red[warp][c0] = d0;
+    red[warp][c1] = d1;
+    __syncthreads();
+    for (int c = threadIdx.x; c < R; c += kThreads) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; w++) s += red[w][c];
+        partial[(int64_t)blockIdx.x * MAXR + c] = s;
+    }
+}
+
+// lambda_r = sqrt(Ghat_rr); G_n = Ghat / (lambda lambda^T); inner_r.
+__global__ void __launch_bounds__(kThreads) k_finish_mode(const double *__restrict__ partial, int nblocks, int R,
+                                                          double *__restrict__ lambda, double *__restrict__ G,
+                                                          double *__restrict__ inner) {
+    __shared__ double lam[MAXR];
+    for (int r = threadIdx.x; r < R; r += kThreads) {
+        const double l = sqrt(G[r * R + r]);
+        lam[r] = l;
+        lambda[r] = l;
+        double s = 0.0;
+        for (int b = 0; b < nblocks; b++) s += partial[(int64_t)b * MAXR + r];
+        inner[r] = l > 0.0 ? s / l : 0.0;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < R * R; idx += kThreads) {
+        const int r = idx / R, s = idx % R;
+        const double d = lam[r] * lam[s];
+        G[idx] = d > 0.0 ? G[idx] / d : 0.0;
+    }
+}
+
+template <typename C, typename FT> __device__ __forceinline__ FT store_as(C x);
+template <> __device__ __forceinline__ double store_as<double, double>(double x) { return x; }
+template <> __device__ __forceinline__ float store_as<float, float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 store_as<float, __nv_bfloat16>(float x) {
+    return __float2bfloat16_rn(x);
+}
+
+template <typename C, typename FT>
+__global__ void __launch_bounds__(kThreads) k_scale_store(const C *__restrict__ Mh, int64_t I, int R,
+                                                          const double *__restrict__ lambda, FT *__restrict__ A) {
+    __shared__ C lam[MAXR];
+    for (int r = threadIdx.x; r < R; r += kThreads) lam[r] = (C)lambda[r];
+    __syncthreads();
+    const int64_t tot = I * R;
+    for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * kThreads) {
+        const int r = (int)(idx % R);
+        const C l = lam[r];
+        const C v = Mh[idx];
+        A[idx] = store_as<C, FT>(l > C(0) ? v / l : v);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_fit(const double *__restrict__ G_all, int N, int R,
+                                                  const double *__restrict__ lambda, const double *__restrict__ inner,
+                                                  const double *__restrict__ normX2, double *__restrict__ fit) {
+    __shared__ double red[kThreads / 32];
+    double s = 0.0;
+    const int RR = R * R;
+    for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
+        double h = 1.0;
+        for (int k = 0; k < N; k++) h *= G_all[(int64_t)k * RR + idx];
+        s += lambda[idx / R] * h * lambda[idx % R];
+    }
+    for (int r = threadIdx.x; r < R; r += kThreads) s -= 2.0 * lambda[r] * inner[r];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; w++) t += red[w];
+        const double res = normX2[0] + t;
+        fit[0] = 1.0 - sqrt(res > 0.0 ? res : 0.0) / sqrt(normX2[0]);
+    }
+}
+
+inline int rows_grid(int64_t I, int rows_per_block) {
+    int64_t g = (I + rows_per_block - 1) / rows_per_block;
+    if (g > GR_BLOCKS) g = GR_BLOCKS;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+size_t dense_scratch_doubles(int R) {
+    (void)R;
+    return (size_t)GR_BLOCKS * MAXPAIRS + (size_t)GR_BLOCKS * MAXR + 64;
+}
+
+cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, cudaStream_t st) {
+    if (R < 1 || R > MAXR) return cudaErrorInvalidValue;
+    if (I == 0) return cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
+    const int g = rows_grid(I, GR_ROWS);
+    switch (dtype) {
+    case RELATE_F64: k_gram_partial<double><<<g, kThreads, 0, st>>>((const double *)A, I, R, scratch); break;
+    case RELATE_F32: k_gram_partial<float><<<g, kThreads, 0, st>>>((const float *)A, I, R, scratch); break;
+    default: k_gram_partial<__nv_bfloat16><<<g, kThreads, 0, st>>>((const __nv_bfloat16 *)A, I, R, scratch); break;
+    }
+    const int npairs = R * (R + 1) / 2;
+    k_gram_reduce<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, st>>>(scratch, g, R, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv, float *Vinv32, int *status,
+                             cudaStream_t st) {
+    const size_t smem = 2 * sizeof(double) * MAXR * (MAXR + 1);
+    cudaError_t e = cudaFuncSetAttribute(k_normal_eq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_normal_eq<<<1, kThreads, smem, st>>>(G_all, N, n, R, Vinv, Vinv32, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv, const float *Vinv32,
+                              double *scratch, cudaStream_t st) {
+    const int g = rows_grid(I, kThreads / 32);
+    double *partial = scratch + (size_t)GR_BLOCKS * MAXPAIRS;
+    if (acc_dtype == RELATE_F64)
+        k_solve_rows<double><<<g, kThreads, 0, st>>>((double *)M, I, R, Vinv, partial);
+    else
+        k_solve_rows<float><<<g, kThreads, 0, st>>>((float *)M, I, R, Vinv32, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_mode(const double *scratch, int64_t I, int R, double *lambda, double *G_n, double *inner,
+                               cudaStream_t st) {
+    const int g = rows_grid(I, kThreads / 32);
+    const double *partial = scratch + (size_t)GR_BLOCKS * MAXPAIRS;
+    k_finish_mode<<<1, kThreads, 0, st>>>(partial, g, R, lambda, G_n, inner);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_store(const void *Mh, int64_t I, int R, int acc_dtype, const double *lambda, void *A,
+                               int factor_dtype, cudaStream_t st) {
+    if (I == 0) return cudaSuccess;
+    int64_t g64 = (I * R + kThreads - 1) / kThreads;
+    const int g = (int)(g64 > 152 * 16 ? 152 * 16 : g64);
+    if (factor_dtype == RELATE_F64)
+        k_scale_store<double, double><<<g, kThreads, 0, st>>>((const double *)Mh, I, R, lambda, (double *)A);
+    else if (factor_dtype == RELATE_F32)
+        k_scale_store<float, float><<<g, kThreads, 0, st>>>((const float *)Mh, I, R, lambda, (float *)A);
+    else
+        k_scale_store<float, __nv_bfloat16><<<g, kThreads, 0, st>>>((const float *)Mh, I, R, lambda,
+                                                                     (__nv_bfloat16 *)A);
+    (void)acc_dtype;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const double *G_all, int N, int R, const double *lambda, const double *inner,
+                       const double *normX2, double *fit, cudaStream_t st) {
+    k_fit<<<1, kThreads, 0, st>>>(G_all, N, R, lambda, inner, normX2, fit);
+    return cudaGetLastError();
+}
+
+}  // namespace relate

@@ -1,0 +1,162 @@
+// internal.cuh -- declarations shared by the library's translation units.
+// Nothing here is part of the public ABI (include/relate.h is).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "relate.h"
+
+#define RELATE_VERSION_STRING "relate-gb300 0.1.0 (sm_103a)"
+
+namespace relate {
+
+constexpr int kMaxModes = RELATE_MAX_MODES;
+constexpr int kMaxRuns = RELATE_MAX_KEY_BITS;
+constexpr int kThreads = 256;  // threads per block of the streaming kernels
+
+// A maximal run of bits that one mode contributes to the position p:
+// bits [src, src+len) of i_mode land in bits [dst, dst+len) of p
+// (Sec. 3.3.1-3.3.2: mode a_t gives its next low bit to b^t, so each mode's
+// bits keep their order and consecutive b^t of one mode form a run).
+struct BitRuns {
+    int nruns;
+    int mode_begin[kMaxModes + 1];  // runs grouped by mode: [mode_begin[m], mode_begin[m+1])
+    uint8_t src[kMaxRuns];
+    uint8_t dst[kMaxRuns];
+    uint8_t len[kMaxRuns];
+    int field_off[kMaxModes];        // bit offset of mode m's field in the stored word
+};
+
+// Field decoding for the stored word (coordinates as concatenated fields).
+struct Fields {
+    int shift[kMaxModes];
+    uint32_t mask[kMaxModes];
+};
+
+// 128-bit stored word / key, little-endian 32-bit limbs, 16-byte aligned.
+struct __align__(16) W128 {
+    uint64_t lo, hi;
+};
+
+template <int KW> struct WordT;
+template <> struct WordT<1> { using T = uint32_t; };
+template <> struct WordT<2> { using T = unsigned long long; };
+template <> struct WordT<4> { using T = W128; };
+
+// ---------------------------------------------------------------- encode
+// Temporary device memory the radix sort needs for n keys of KW limbs.
+size_t radix_sort_temp_bytes(int64_t n);
+
+// Builds p for every nonzero (K1) and the identity payload; sets *err to 1
+// if some coordinate is out of range.
+cudaError_t launch_build_keys(int KW, const uint32_t *coords, const uint64_t *dims_dev, int64_t n,
+                              int N, const BitRuns &runs, void *keys, uint32_t *idx,
+                              uint32_t *err, cudaStream_t st);
+
+// Stable LSD radix sort of (key, payload) over bits [0, lp) (K2). The
+// result ends in (keys, vals) or (keys_alt, vals_alt); *in_alt tells which.
+cudaError_t radix_sort_pairs(int KW, void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt,
+                             int64_t n, int lp, void *temp, size_t temp_bytes, cudaStream_t st,
+                             bool *in_alt);
+
+// p (sorted) -> stored word with concatenated coordinate fields.
+cudaError_t launch_make_words(int KW, const void *keys, int64_t n, const BitRuns &runs, void *words,
+                              cudaStream_t st);
+
+// stored word -> p (for export / tests).
+cudaError_t launch_words_to_keys(int KW, const void *words, int64_t n, const BitRuns &runs,
+                                 uint64_t *keys_out2, cudaStream_t st);
+
+// stored word -> coordinates SoA.
+cudaError_t launch_decode_words(int KW, const void *words, int64_t n, int N, const Fields &f,
+                                uint32_t *coords_out, cudaStream_t st);
+
+// vals_out[j] = vals_in[perm[j]] (elem_bytes 4 or 8).
+cudaError_t launch_gather(const void *vals_in, const uint32_t *perm, int64_t n, int elem_bytes,
+                          void *vals_out, cudaStream_t st);
+
+struct CountPtrs {
+    uint32_t *p[kMaxModes];
+    uint64_t len[kMaxModes];  // entries of p[m] (= I_m); larger fields are not counted
+};
+
+// Per-partition [lo, hi] per mode, per-mode run counts and histograms (K3).
+// runs: N uint64 (accumulated), counts: per mode dims[m] uint32 (zeroed by caller).
+cudaError_t launch_partition_stats(int KW, const void *words, int64_t n, int N, const Fields &f,
+                                   int64_t S, uint32_t *plo, uint32_t *phi,
+                                   unsigned long long *runs, const CountPtrs &counts,
+                                   cudaStream_t st);
+
+// distinct / maxcount of a histogram (accumulated into out[0], out[1]).
+cudaError_t launch_hist_summary(const uint32_t *counts, uint64_t len, unsigned long long *out2,
+                                cudaStream_t st);
+
+// sum of v^2 in FP64 (deterministic two-level reduction); partial: >= 1024 doubles
+cudaError_t launch_sum_squares(const void *vals, int64_t n, int elem_bytes, double *partial,
+                               double *out, cudaStream_t st);
+
+// ---------------------------------------------------------------- mttkrp
+struct MttkrpArgs {
+    const void *words;
+    const void *vals;
+    int64_t nnz;
+    int64_t S;
+    int64_t P;
+    int N;
+    int mode;
+    Fields fields;
+    const void *factors[kMaxModes];
+    int R;
+    void *out;
+    uint64_t In;
+    int strategy;            // relate_conflict_t (resolved, not AUTO)
+    const uint32_t *plo;
+    const uint32_t *phi;
+    int window_rows;         // SEGMENTED: rows that fit the shared window
+};
+
+// Launches K5/K6/K7 for the given dtypes. factor_dtype / val_dtype are
+// relate_dtype_t. smem_budget: bytes available for shared accumulators.
+cudaError_t launch_mttkrp(const MttkrpArgs &a, int KW, int factor_dtype, int val_dtype,
+                          int smem_budget, int num_sms, cudaStream_t st);
+
+// Bytes of shared memory one row of the output accumulator takes.
+int mttkrp_acc_bytes(int factor_dtype);
+
+// ---------------------------------------------------------------- dense
+// Scratch the dense kernels need (doubles): partial sums for the Gram and
+// the row passes.
+size_t dense_scratch_doubles(int R);
+
+// G = A^T A, FP64 out (R x R) via per-block partials in `scratch`.
+cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G,
+                        cudaStream_t st);
+
+// V = Hadamard_{k != n} G_k; Cholesky; Vinv (FP64 and FP32 copies).
+// status[0] |= 1 on ridge retry, status[1] = 1 if not PD after the retry.
+cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv,
+                             float *Vinv32, int *status, cudaStream_t st);
+
+// Row pass 1: in place, M (I x R, acc dtype) <- M Vinv; per-block partials of
+// the Gram of the result and of <M_old(:,r), result(:,r)>.
+cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv,
+                              const float *Vinv32, double *scratch, cudaStream_t st);
+
+// Reduces the solve partials into lambda, G_n (normalised Gram) and the fit
+// inner products.
+cudaError_t launch_finish_mode(const double *scratch, int64_t I, int R, double *lambda,
+                               double *G_n, double *inner, cudaStream_t st);
+
+// Row pass 2: A_n = Mhat / lambda, stored in the factor dtype.
+cudaError_t launch_scale_store(const void *Mhat, int64_t I, int R, int acc_dtype,
+                               const double *lambda, void *A, int factor_dtype, cudaStream_t st);
+
+// fit after the last mode (device scalar out[0]).
+cudaError_t launch_fit(const double *G_all, int N, int R, const double *lambda, const double *inner,
+                       const double *normX2, double *fit, cudaStream_t st);
+
+}  // namespace relate

@@ -150,23 +150,41 @@ def make_coords(spec: TensorSpec) -> np.ndarray:
             tables.append(label_permutation(spec.seed, n, int(spec.dims[n])))
     if not spec.distinct:
         return _draw_coords(spec, 0, spec.nnz, tables)
-    M = int(spec.nnz * 1.25) + 1024
-    for _ in range(40):
-        c = _draw_coords(spec, 0, M, tables)
+    # Take draws in counter order, keeping the first occurrence of each tuple,
+    # in batches; `seen` holds the kept tuples' keys sorted for lookups.
+    kept_parts, seen, have, cursor = [], None, 0, 0
+    batch = int(spec.nnz * 1.1) + 1024
+    for _ in range(200):
+        c = _draw_coords(spec, cursor, cursor + batch, tables)
+        cursor += batch
         keys = _dedup_keys(c, spec.dims)
-        order = np.lexsort(tuple(reversed(keys))) if len(keys) > 1 else np.argsort(keys[0], kind="stable")
-        dup = np.ones(M, dtype=bool)
-        for k in keys:
-            ks = k[order]
-            dup[1:] &= ks[1:] == ks[:-1]
-        dup[0] = False
-        first = np.ones(M, dtype=bool)
-        first[order[dup]] = False
-        kept = np.nonzero(first)[0]
-        if kept.shape[0] >= spec.nnz:
-            return np.ascontiguousarray(c[:, kept[:spec.nnz]])
-        M = int(M * 1.6)
+        if len(keys) == 1:
+            k = keys[0]
+        else:  # pack (hi, lo) into a structured view comparable as a pair
+            k = np.empty(c.shape[1], dtype=[("h", np.uint64), ("l", np.uint64)])
+            k["h"], k["l"] = keys[0], keys[1] if len(keys) == 2 else _fold(keys[1:])
+        order = np.argsort(k, kind="stable")
+        ks = k[order]
+        first = np.ones(c.shape[1], dtype=bool)
+        first[order[1:][ks[1:] == ks[:-1]]] = False
+        if seen is not None:
+            pos = np.searchsorted(seen, k)
+            pos = np.minimum(pos, len(seen) - 1)
+            first &= seen[pos] != k
+        idx = np.nonzero(first)[0][: spec.nnz - have]
+        kept_parts.append(c[:, idx])
+        have += idx.shape[0]
+        if have >= spec.nnz:
+            return np.ascontiguousarray(np.concatenate(kept_parts, axis=1))
+        seen = np.sort(k[idx]) if seen is None else np.sort(np.concatenate([seen, k[idx]]))
+        batch = max(int((spec.nnz - have) * 2.0), 1024)
     raise ValueError(f"{spec.name}: could not draw {spec.nnz} distinct coordinates")
+
+
+def _fold(keys):
+    if len(keys) != 1:
+        raise ValueError("tensor too large for the distinct-coordinate check")
+    return keys[0]
 
 
 def make_values(spec: TensorSpec) -> np.ndarray:

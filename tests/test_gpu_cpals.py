@@ -1,0 +1,77 @@
+"""GPU CP-ALS vs the CPU oracle's CP-ALS (standard ALS, Sec. 2.2 context).
+
+FP64: fit trace within 1e-9 of the oracle's, factors and lambda close.
+Mixed precision (FP32 / BF16 factors, FP32 MTTKRP, FP64 Cholesky): final
+fit within 1e-3 of the FP64 oracle run from the same initial factors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2509_00280_gb300 as rl
+from gpu_util import DEV, encode_dev, factors_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fp64_uniform_1M_10_iters():
+    w = synth.WORKLOADS["uniform3d-1000x1000x1000-1M"]
+    spec = w["spec"]
+    c, v = synth.make_tensor(spec)
+    R = w["R"]
+    fs = synth.init_factors(spec.dims, R, seed=0)
+    ref = oracle.cpals(c, v, spec.dims, R, 10, 0.0, fs)
+    h = encode_dev(c, v, spec.dims, factor_dtype="f64")
+    dfs = factors_dev(fs, "f64")
+    res = rl.relate_cpals(h, R, 10, 0.0, dfs)
+    assert res["iters"] == 10 and res["status"] == 0
+    assert np.max(np.abs(res["fit_trace"] - ref["fit_trace"])) <= 1e-9
+    np.testing.assert_allclose(res["lam"], ref["lam"], rtol=1e-7)
+    for f, g in zip(dfs, ref["factors"]):
+        assert np.linalg.norm(f.cpu().numpy() - g) <= 1e-6 * np.linalg.norm(g)
+    h.close()
+
+
+def test_planted_rank3_recovered_on_gpu():
+    rng = np.random.default_rng(21)
+    dims = (12, 10, 8)
+    true = [rng.random((d, 3)) + 0.1 for d in dims]
+    X = np.einsum("ar,br,cr,r->abc", *true, np.array([3.0, 2.0, 1.0]))
+    c = np.stack(np.nonzero(X)).astype(np.uint32)
+    v = X[tuple(c)]
+    init = [rng.random((d, 3)) for d in dims]
+    h = encode_dev(c, v, dims, factor_dtype="f64")
+    res = rl.relate_cpals(h, 3, 1000, 0.0, factors_dev(init, "f64"))
+    assert res["fit"] > 0.9999
+    h.close()
+
+
+@pytest.mark.parametrize("fdt", ["f32", "bf16"])
+def test_mixed_precision_fit_within_1e3(fdt):
+    spec = synth.scaled(synth.WORKLOADS["zipf3d-200Kx200Kx5K-50M"]["spec"], 500_000, dims=(20000, 20000, 500))
+    c, v = synth.make_tensor(spec)
+    R = 16
+    fs = synth.init_factors(spec.dims, R, seed=0, dtype=np.float32)
+    iters = 8
+    ref = oracle.cpals(c, v.astype(np.float64), spec.dims, R, iters, 0.0, [f.astype(np.float64) for f in fs])
+    h = encode_dev(c, v, spec.dims, factor_dtype=fdt)
+    res = rl.relate_cpals(h, R, iters, 0.0, factors_dev(fs, fdt))
+    assert res["iters"] == iters
+    assert abs(res["fit"] - ref["fit_trace"][-1]) <= 1e-3, (res["fit"], ref["fit_trace"][-1])
+    h.close()
+
+
+def test_tolerance_stop_and_warm_restart():
+    spec = synth.scaled(synth.WORKLOADS["uniform3d-1000x1000x1000-1M"]["spec"], 50_000, dims=(100, 120, 90))
+    c, v = synth.make_tensor(spec)
+    fs = synth.init_factors(spec.dims, 4, seed=0)
+    h = encode_dev(c, v, spec.dims, factor_dtype="f64")
+    dfs = factors_dev(fs, "f64")
+    r1 = rl.relate_cpals(h, 4, 200, 1e-4, dfs)
+    assert r1["iters"] < 200
+    # resume from the returned factors (checkpoint = the caller-owned factors)
+    r2 = rl.relate_cpals(h, 4, 2, 0.0, dfs)
+    assert r2["fit"] >= r1["fit"] - 1e-9
+    h.close()
