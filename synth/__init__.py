@@ -26,10 +26,54 @@ available here): power-law modes, a short time-like mode, hyper-sparse dims.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_C_LIB = None
+_C_LOCK = threading.Lock()
+
+
+def _clib():
+    """The multithreaded C helper (synthc.c), compiled on first use; None if
+    no compiler is available (the numpy path then runs)."""
+    global _C_LIB
+    with _C_LOCK:
+        if _C_LIB is None:
+            src = os.path.join(_HERE, "synthc.c")
+            out = os.path.join(_HERE, "_build", "libsynthc.so")
+            try:
+                os.makedirs(os.path.dirname(out), exist_ok=True)
+                if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+                    tmp = out + f".tmp{os.getpid()}"
+                    subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp],
+                                   check=True, capture_output=True)
+                    os.replace(tmp, out)
+                L = ctypes.CDLL(out)
+                P, I64, U64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+                L.synth_base.restype, L.synth_base.argtypes = U64, [U64, U64]
+                L.synth_labels.restype = None
+                L.synth_labels.argtypes = [U64, I64, I64, I, U64, P, P, P, I]
+                L.synth_dedup_new.restype, L.synth_dedup_new.argtypes = P, [I, P, I, U64, I]
+                L.synth_dedup_free.restype, L.synth_dedup_free.argtypes = None, [P]
+                L.synth_dedup_insert.restype, L.synth_dedup_insert.argtypes = I64, [P, P, I64, P]
+                _C_LIB = L
+            except Exception:
+                _C_LIB = False
+        return _C_LIB or None
+
+
+def _threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except Exception:
+        return os.cpu_count() or 1
 
 GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -99,10 +143,21 @@ class TensorSpec:
     extra: dict = field(default_factory=dict)
 
 
-def _draw_coords(spec: TensorSpec, lo: int, hi: int, tables) -> np.ndarray:
-    idx = np.arange(lo, hi, dtype=np.uint64)
+def _draw_coords(spec: TensorSpec, lo: int, hi: int, tables, use_c: bool = True) -> np.ndarray:
     N = len(spec.dims)
     out = np.empty((N, hi - lo), dtype=np.uint32)
+    L = _clib() if use_c else None
+    if L is not None:
+        for n in range(N):
+            d = spec.dists[n]
+            cdf = tables[n] if d[0] == "zipf" else None
+            perm = tables[N + n] if spec.shuffle else None
+            base = L.synth_base(spec.seed, TAG_COORD + n)
+            L.synth_labels(base, lo, hi - lo, 1 if d[0] == "zipf" else 0, int(spec.dims[n]),
+                           cdf.ctypes.data if cdf is not None else None,
+                           perm.ctypes.data if perm is not None else None, out[n].ctypes.data, _threads())
+        return out
+    idx = np.arange(lo, hi, dtype=np.uint64)
     for n in range(N):
         x = stream(spec.seed, TAG_COORD + n, idx)
         d = spec.dists[n]
@@ -139,7 +194,50 @@ def _dedup_keys(coords: np.ndarray, dims) -> list:
     return keys
 
 
-def make_coords(spec: TensorSpec) -> np.ndarray:
+def _split_point(dims) -> int:
+    """Modes [0, split) and [split, N) each have a mixed-radix product < 2^64."""
+    prod, split = 1, 0
+    for n, I in enumerate(dims):
+        if prod * int(I) >= 2 ** 64:
+            break
+        prod *= int(I)
+        split = n + 1
+    rest = 1
+    for I in dims[split:]:
+        rest *= int(I)
+    if rest >= 2 ** 64:
+        raise ValueError("tensor too large for the distinct-coordinate check")
+    return split
+
+
+def _make_coords_c(spec: TensorSpec, tables, L) -> np.ndarray | None:
+    N = len(spec.dims)
+    dims = np.array(spec.dims, dtype=np.uint64)
+    T = _threads()
+    st = L.synth_dedup_new(N, dims.ctypes.data, _split_point(spec.dims), 2 * spec.nnz + 4096, T)
+    if not st:
+        return None
+    try:
+        kept_parts, have, cursor = [], 0, 0
+        batch = int(spec.nnz * 1.1) + 1024
+        for _ in range(200):
+            c = _draw_coords(spec, cursor, cursor + batch, tables)
+            cursor += batch
+            keep = np.zeros(batch, dtype=np.uint8)
+            if L.synth_dedup_insert(st, c.ctypes.data, batch, keep.ctypes.data) < 0 or (keep == 2).any():
+                return None
+            idx = np.nonzero(keep)[0][: spec.nnz - have]
+            kept_parts.append(c[:, idx])
+            have += idx.shape[0]
+            if have >= spec.nnz:
+                return np.ascontiguousarray(np.concatenate(kept_parts, axis=1))
+            batch = max(int((spec.nnz - have) * 2.0), 1024)
+        raise ValueError(f"{spec.name}: could not draw {spec.nnz} distinct coordinates")
+    finally:
+        L.synth_dedup_free(st)
+
+
+def make_coords(spec: TensorSpec, use_c: bool = True) -> np.ndarray:
     N = len(spec.dims)
     tables = []
     for n in range(N):
@@ -149,13 +247,18 @@ def make_coords(spec: TensorSpec) -> np.ndarray:
         for n in range(N):
             tables.append(label_permutation(spec.seed, n, int(spec.dims[n])))
     if not spec.distinct:
-        return _draw_coords(spec, 0, spec.nnz, tables)
+        return _draw_coords(spec, 0, spec.nnz, tables, use_c)
+    L = _clib() if use_c else None
+    if L is not None:
+        got = _make_coords_c(spec, tables, L)
+        if got is not None:
+            return got
     # Take draws in counter order, keeping the first occurrence of each tuple,
     # in batches; `seen` holds the kept tuples' keys sorted for lookups.
     kept_parts, seen, have, cursor = [], None, 0, 0
     batch = int(spec.nnz * 1.1) + 1024
     for _ in range(200):
-        c = _draw_coords(spec, cursor, cursor + batch, tables)
+        c = _draw_coords(spec, cursor, cursor + batch, tables, use_c=False)
         cursor += batch
         keys = _dedup_keys(c, spec.dims)
         if len(keys) == 1:
@@ -239,6 +342,11 @@ WORKLOADS = {
     # skewed 3-mode: Zipf 1.2 on every mode, lognormal FP32 values
     "zipf3d-200Kx200Kx5K-50M": dict(
         spec=TensorSpec("zipf3d-200Kx200Kx5K-50M", (200_000, 200_000, 5_000), 50_000_000,
+                        (("zipf", 1.2),) * 3, values="lognormal", value_dtype="f32", seed=2),
+        R=32, iters=25, factor_dtype="f32"),
+    # the same recipe at 20M nonzeros (stream 240 MB > L2): small case for profiler captures
+    "zipf3d-200Kx200Kx5K-20M": dict(
+        spec=TensorSpec("zipf3d-200Kx200Kx5K-20M", (200_000, 200_000, 5_000), 20_000_000,
                         (("zipf", 1.2),) * 3, values="lognormal", value_dtype="f32", seed=2),
         R=32, iters=25, factor_dtype="f32"),
     # 4-mode with a short time-like mode
