@@ -210,6 +210,12 @@ int relate_get_partitions(relate_handle_t h, uint32_t *lo, uint32_t *hi, void *s
  * within blocks of rows and in FP64 across blocks. Async on stream. */
 int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream);
 
+/* Synchronises `stream` and reports whether any kernel of this handle gave
+ * up a bounded device wait since the last call (RELATE_ERR_TIMEOUT; the flag
+ * is then cleared). The MTTKRP kernel waits on its own tile copies with an
+ * iteration limit instead of spinning forever. Returns RELATE_OK otherwise. */
+int relate_sync_status(relate_handle_t h, void *stream);
+
 /* Frees the handle and all its device memory (synchronises its stream). */
 void relate_free(relate_handle_t h);
 

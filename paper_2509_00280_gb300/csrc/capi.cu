@@ -58,7 +58,9 @@ struct relate_handle_s {
     uint32_t *d_perm = nullptr;
     uint32_t *d_plo = nullptr, *d_phi = nullptr;
     uint32_t *d_counts[kMaxModes] = {};
+    uint32_t *d_hot_rows[kMaxModes] = {};
     double *d_normX2 = nullptr;
+    int *d_err = nullptr;  // device error flags of this handle's kernels
     uint64_t runs_n[kMaxModes] = {}, distinct[kMaxModes] = {}, maxcount[kMaxModes] = {};
 
     // CP-ALS workspace (grown on demand)
@@ -72,11 +74,13 @@ struct relate_handle_s {
     ~relate_handle_s() {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
-        void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_M, d_scratch, d_G, d_Vinv,
+        void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_err, d_M, d_scratch, d_G, d_Vinv,
                         d_lambda, d_inner, d_fit, d_Vinv32, d_status};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         for (auto *p : d_counts)
+            if (p) cudaFree(p);
+        for (auto *p : d_hot_rows)
             if (p) cudaFree(p);
     }
 };
@@ -87,8 +91,8 @@ relate_conflict_t resolve_conflict(const relate_handle_s *h, int mode, int R) {
     if (h->conflict[mode] != RELATE_CONFLICT_AUTO) return h->conflict[mode];
     const int accb = mttkrp_acc_bytes(h->factor_dtype);
     const uint64_t priv_bytes = h->dims[mode] * (uint64_t)R * accb;
-    // whole-output privatisation when it leaves room for >= 2 blocks per SM
-    if (priv_bytes <= 96u * 1024u && priv_bytes <= (uint64_t)h->smem_budget) return RELATE_CONFLICT_PRIVATIZED;
+    // whole-output privatisation when it leaves room for two blocks per SM
+    if (priv_bytes <= 32u * 1024u) return RELATE_CONFLICT_PRIVATIZED;
     const double reuse = h->distinct[mode] ? (double)h->nnz / (double)h->distinct[mode] : 0.0;
     const double mean_run = h->runs_n[mode] ? (double)h->nnz / (double)h->runs_n[mode] : 0.0;
     // "minimum fiber reuse 8" (Sec. 4.1.3) for reduction-based synchronisation
@@ -203,10 +207,10 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
     a.In = h->dims[mode];
     a.plo = h->d_plo;
     a.phi = h->d_phi;
+    a.hot_rows = h->d_hot_rows[mode];
+    a.err = h->d_err;
     a.strategy = resolve_conflict(h, mode, R);
     const int accb = mttkrp_acc_bytes(h->factor_dtype);
-    if (a.strategy == RELATE_CONFLICT_PRIVATIZED && h->dims[mode] * (uint64_t)R * accb > (uint64_t)h->smem_budget)
-        a.strategy = RELATE_CONFLICT_SEGMENTED;  // explicit request that does not fit
     cudaError_t e = cudaMemsetAsync(out, 0, h->dims[mode] * (size_t)R * accb, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp memset");
     e = launch_mttkrp(a, h->KW, h->factor_dtype, h->val_dtype, h->smem_budget, h->num_sms, st);
@@ -353,16 +357,20 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
              *idx_alt = nullptr, *sort_tmp = nullptr, *d_dims = nullptr, *d_small = nullptr;
         const size_t sort_bytes = radix_sort_temp_bytes(nnz);
         // persistent encoding arrays
-        if ((e = cudaMalloc(&h->d_words, nnz * kb + 16)) != cudaSuccess ||
-            (e = cudaMalloc(&h->d_vals, nnz * vb + 16)) != cudaSuccess ||
+        // 64 bytes of tail padding: tile copies round their size up to 16 bytes
+        if ((e = cudaMalloc(&h->d_words, nnz * kb + 64)) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_vals, nnz * vb + 64)) != cudaSuccess ||
             (e = cudaMalloc((void **)&h->d_plo, (h->P + 1) * N * 4)) != cudaSuccess ||
             (e = cudaMalloc((void **)&h->d_phi, (h->P + 1) * N * 4)) != cudaSuccess ||
-            (e = cudaMalloc((void **)&h->d_normX2, 64)) != cudaSuccess) {
+            (e = cudaMalloc((void **)&h->d_normX2, 64)) != cudaSuccess ||
+            (e = cudaMalloc((void **)&h->d_err, 16)) != cudaSuccess ||
+            (e = cudaMemsetAsync(h->d_err, 0, 16, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: allocation");
             goto done;
         }
         for (int m = 0; m < N; m++)
-            if ((e = cudaMalloc((void **)&h->d_counts[m], h->dims[m] * 4)) != cudaSuccess) {
+            if ((e = cudaMalloc((void **)&h->d_counts[m], h->dims[m] * 4)) != cudaSuccess ||
+                (e = cudaMalloc((void **)&h->d_hot_rows[m], kHotMax * 4)) != cudaSuccess) {
                 rc = cuda_fail(e, "relate_encode: allocation");
                 goto done;
             }
@@ -441,6 +449,21 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
             rc = cuda_fail(e, "relate_encode: norm");
             goto done;
         }
+        {
+            uint64_t maxI = 0;
+            for (int m = 0; m < N; m++) maxI = h->dims[m] > maxI ? h->dims[m] : maxI;
+            void *hot_tmp = nullptr;
+            if ((e = tmp.alloc(&hot_tmp, hot_table_temp_bytes(maxI))) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: hot-row table");
+                goto done;
+            }
+            for (int m = 0; m < N; m++)
+                if ((e = launch_hot_table(h->d_counts[m], h->dims[m], h->d_hot_rows[m], hot_tmp, st)) !=
+                    cudaSuccess) {
+                    rc = cuda_fail(e, "relate_encode: hot-row table");
+                    goto done;
+                }
+        }
         unsigned long long host_small[1 + 3 * kMaxModes];
         if ((e = cudaMemcpyAsync(host_small, d_small, sizeof(host_small), cudaMemcpyDeviceToHost, st)) !=
                 cudaSuccess ||
@@ -503,7 +526,7 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
             return cuda_fail(e, "relate_cpals: initial Gram");
     double prev = 0.0, fit = 0.0;
     int done = 0;
-    int hstatus[2] = {0, 0};
+    int hstatus[3] = {0, 0, 0};
     for (int it = 1; it <= iters; it++) {
         for (int n = 0; n < N; n++) {
             const int64_t In = (int64_t)h->dims[n];
@@ -522,11 +545,21 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
         if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess)
             return cuda_fail(e, "relate_cpals: fit");
         if ((e = cudaMemcpyAsync(&fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(hstatus, h->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hstatus, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hstatus + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_fail(e, "relate_cpals: fit to host");
         done = it;
         if (info && info->fit_trace) info->fit_trace[it - 1] = fit;
+        if (hstatus[2]) {
+            cudaMemsetAsync(h->d_err, 0, 16, st);
+            if (info) {
+                info->fit = fit;
+                info->iters = done;
+                info->status = RELATE_ERR_TIMEOUT;
+            }
+            return fail(RELATE_ERR_TIMEOUT, "relate_cpals: a bounded device wait timed out (iteration %d)", it);
+        }
         if (hstatus[1]) break;
         if (it > 1 && (fit - prev < tol && prev - fit < tol)) break;
         prev = fit;
@@ -643,6 +676,24 @@ int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G
     cudaError_t e2 = cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_gram: launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "relate_gram: free");
+    return RELATE_OK;
+}
+
+int relate_sync_status(relate_handle_t h, void *stream) {
+    g_err[0] = 0;
+    if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_sync_status: NULL handle");
+    const cudaStream_t st = (cudaStream_t)stream;
+    int flag = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "relate_sync_status");
+    if (flag) {
+        if ((e = cudaMemsetAsync(h->d_err, 0, 16, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_fail(e, "relate_sync_status: clear");
+        return fail(RELATE_ERR_TIMEOUT, "relate_sync_status: a bounded device wait timed out");
+    }
     return RELATE_OK;
 }
 

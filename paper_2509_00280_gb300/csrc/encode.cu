@@ -479,6 +479,24 @@ __global__ void k_sum_fixed(const double *__restrict__ partial, int np, double *
     }
 }
 
+// hot-row table: sort rows by decreasing population (stable), keep kHotMax
+__global__ void __launch_bounds__(kThreads) k_count_keys(const uint32_t *__restrict__ counts, uint64_t I,
+                                                         uint32_t *__restrict__ keys, uint32_t *__restrict__ idx) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (uint64_t)gridDim.x * blockDim.x) {
+        keys[i] = 0xffffffffu - counts[i];
+        idx[i] = (uint32_t)i;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_hot_rows(const uint32_t *__restrict__ sorted_keys,
+                                                       const uint32_t *__restrict__ sorted_idx, uint64_t I,
+                                                       uint32_t *__restrict__ hot_rows) {
+    const int j = threadIdx.x + blockIdx.x * blockDim.x;
+    if (j >= kHotMax) return;
+    // count > 0 (key = ~count); 0xffffffff marks an unused entry
+    hot_rows[j] = ((uint64_t)j < I && sorted_keys[j] != 0xffffffffu) ? sorted_idx[j] : 0xffffffffu;
+}
+
 inline int grid_for(int64_t n, int per_block = kThreads, int cap = 152 * 32) {
     int64_t g = (n + per_block - 1) / per_block;
     if (g < 1) g = 1;
@@ -616,6 +634,24 @@ cudaError_t launch_partition_stats(int KW, const void *words, int64_t n, int N, 
 cudaError_t launch_hist_summary(const uint32_t *counts, uint64_t len, unsigned long long *out2, cudaStream_t st) {
     if (len == 0) return cudaSuccess;
     k_hist_summary<<<grid_for((int64_t)len), kThreads, 0, st>>>(counts, len, out2);
+    return cudaGetLastError();
+}
+
+size_t hot_table_temp_bytes(uint64_t I) {
+    return 16 * (size_t)I + radix_sort_temp_bytes((int64_t)I) + 64;
+}
+
+cudaError_t launch_hot_table(const uint32_t *counts, uint64_t I, uint32_t *hot_rows, void *temp, cudaStream_t st) {
+    uint32_t *keys = reinterpret_cast<uint32_t *>(temp);
+    uint32_t *idx = keys + I;
+    uint32_t *keys2 = idx + I;
+    uint32_t *idx2 = keys2 + I;
+    void *sort_tmp = idx2 + I;
+    k_count_keys<<<grid_for((int64_t)I), kThreads, 0, st>>>(counts, I, keys, idx);
+    bool in_alt = false;
+    cudaError_t e = rs_passes<uint32_t>(keys, idx, keys2, idx2, (int64_t)I, 32, sort_tmp, st, &in_alt);
+    if (e != cudaSuccess) return e;
+    k_hot_rows<<<1, kHotMax, 0, st>>>(in_alt ? keys2 : keys, in_alt ? idx2 : idx, I, hot_rows);
     return cudaGetLastError();
 }
 

@@ -116,8 +116,25 @@ struct MttkrpArgs {
     int strategy;            // relate_conflict_t (resolved, not AUTO)
     const uint32_t *plo;
     const uint32_t *phi;
-    int window_rows;         // SEGMENTED: rows that fit the shared window
+    const uint32_t *hot_rows;  // kHotMax rows of the mode, most populated first (0xffffffff = unused)
+    int hot_n;                 // hot rows cached in shared memory by this launch
+    int vals_f64;              // values stored as FP64 (else FP32)
+    int *err;                  // device flag: bit 0 = a bounded wait timed out
+    // record slot j of a decoded nonzero: slot 0 = the output mode, slots
+    // 1..N-1 = the other modes in increasing order (filled by the launcher)
+    int rshift[kMaxModes];
+    uint32_t rmask[kMaxModes];
+    const void *rfac[kMaxModes];
 };
+
+// Upper bound of hot (most populated) rows per mode kept in shared memory.
+constexpr int kHotMax = 256;
+
+// Hot rows of one mode from its histogram: the kHotMax most populated rows
+// (ties by row id), most populated first; 0xffffffff pads modes with fewer
+// populated rows. temp must hold hot_table_temp_bytes(I).
+size_t hot_table_temp_bytes(uint64_t I);
+cudaError_t launch_hot_table(const uint32_t *counts, uint64_t I, uint32_t *hot_rows, void *temp, cudaStream_t st);
 
 // Launches K5/K6/K7 for the given dtypes. factor_dtype / val_dtype are
 // relate_dtype_t. smem_budget: bytes available for shared accumulators.

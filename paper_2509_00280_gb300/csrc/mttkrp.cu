@@ -19,28 +19,58 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
     for (int k = 0; k < a.N; k++)
         if (k != a.mode && (reinterpret_cast<uintptr_t>(a.factors[k]) % 16) != 0) vec_ok = false;
 
-    size_t smem = 0;
-    int per_sm = kThreads == 256 ? 8 : 2048 / kThreads;  // resident blocks without shared accumulators
-    if (a.strategy == RELATE_CONFLICT_PRIVATIZED) {
-        smem = (size_t)a.In * a.R * accb;
-        if (smem > (size_t)smem_budget) return cudaErrorInvalidValue;
-        per_sm = (int)((228 * 1024) / (smem + 1024));
-        if (per_sm < 1) per_sm = 1;
-        if (per_sm > 8) per_sm = 8;
-    } else if (a.strategy == RELATE_CONFLICT_SEGMENTED) {
-        // a window of up to ~24 KB keeps 8 blocks resident per SM
-        int rows = (24 * 1024) / (a.R * accb);
-        if (rows < 1) rows = 1;
-        a.window_rows = rows;
-        smem = (size_t)rows * a.R * accb;
+    a.vals_f64 = val_dtype == RELATE_F64;
+    {
+        int j = 1;
+        a.rshift[0] = a.fields.shift[a.mode];
+        a.rmask[0] = a.fields.mask[a.mode];
+        a.rfac[0] = nullptr;
+        for (int k = 0; k < a.N; k++) {
+            if (k == a.mode) continue;
+            a.rshift[j] = a.fields.shift[k];
+            a.rmask[j] = a.fields.mask[k];
+            a.rfac[j] = a.factors[k];
+            j++;
+        }
+        for (; j < kMaxModes; j++) {
+            a.rshift[j] = 0;
+            a.rmask[j] = 0;
+            a.rfac[j] = nullptr;
+        }
     }
+    const size_t tile = mk::tile_bytes_for(a.N, KW, factor_dtype, vec_ok);
+    size_t acc_bytes = 0;
+    if (a.strategy == RELATE_CONFLICT_PRIVATIZED && (size_t)a.In * a.R * accb + 16 + tile > (size_t)smem_budget)
+        a.strategy = RELATE_CONFLICT_SEGMENTED;  // the whole output does not fit: sort tiles instead
+    if (a.strategy == RELATE_CONFLICT_PRIVATIZED) {
+        a.hot_n = 0;
+        acc_bytes = (size_t)a.In * a.R * accb;
+    } else {
+        // hot rows: up to 16 KB of accumulators
+        // Hot rows of unsorted tiles (ATOMIC) accumulate in shared memory:
+        // their runs are short and would contend on the same global lines.
+        // Sorted tiles (SEGMENTED) merge each row's run in registers first,
+        // so their flushes go straight to global memory. Runs are tagged
+        // 0x80000000|slot, so the hot path needs rows < 2^31.
+        int hot = (a.strategy == RELATE_CONFLICT_ATOMIC && a.hot_rows && a.In < (1ull << 31))
+                      ? (16 * 1024) / (a.R * accb) : 0;
+        if (hot > kHotMax) hot = kHotMax;
+        if ((uint64_t)hot > a.In) hot = (int)a.In;
+        a.hot_n = hot;
+        acc_bytes = (size_t)hot * a.R * accb;
+    }
+    const size_t smem = acc_bytes + 16 + tile;
+    int per_sm = (int)((227 * 1024) / (smem + 1024));
+    if (per_sm > 3) per_sm = 3;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t tiles = a.P * ((a.S + mk::kTile - 1) / mk::kTile);
     int64_t grid = (int64_t)num_sms * per_sm;
-    if (grid > a.P) grid = a.P;
+    if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
     switch (factor_dtype) {
-    case RELATE_F64: return mttkrp_f64(a, KW, val_dtype, vec_ok, smem, (int)grid, st);
-    case RELATE_F32: return mttkrp_f32(a, KW, val_dtype, vec_ok, smem, (int)grid, st);
-    default: return mttkrp_bf16(a, KW, val_dtype, vec_ok, smem, (int)grid, st);
+    case RELATE_F64: return mttkrp_f64(a, KW, vec_ok, acc_bytes, (int)grid, st);
+    case RELATE_F32: return mttkrp_f32(a, KW, vec_ok, acc_bytes, (int)grid, st);
+    default: return mttkrp_bf16(a, KW, vec_ok, acc_bytes, (int)grid, st);
     }
 }
 

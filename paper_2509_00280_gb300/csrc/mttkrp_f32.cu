@@ -4,9 +4,8 @@
 
 namespace relate {
 
-cudaError_t mttkrp_f32(const MttkrpArgs &a, int KW, int val_dtype, bool vec_ok, size_t smem, int grid,
-                     cudaStream_t st) {
-    return mk::dispatch_ft<float>(a, KW, val_dtype, vec_ok, smem, grid, st);
+cudaError_t mttkrp_f32(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st) {
+    return mk::dispatch_ft<float>(a, KW, vec_ok, acc_bytes, grid, st);
 }
 
 }  // namespace relate

@@ -129,12 +129,87 @@ template <typename C> struct GAdd<C, 1> {
     static __device__ __forceinline__ void run(C *p, const C (&a)[1]) { atomicAdd(p, a[0]); }
 };
 
-template <int NT, int KW, typename FT, typename VT, int VEC, int VPL>
-__global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs a, const int log2G) {
+// Nonzeros a group keeps in flight: all factor-row loads of U nonzeros are
+// issued before any of them is consumed.
+template <typename FT, int VPL> struct Unroll { static constexpr int U = 4; };
+template <int VPL> struct Unroll<__nv_bfloat16, VPL> { static constexpr int U = 2; };
+
+constexpr int kTile = 2048;       // nonzeros per tile
+constexpr int kItems = kTile / kThreads;
+constexpr int kSortBins = 4096;   // widest row range a tile may span to be sorted
+constexpr int kSnap = 16;         // records a slice boundary may move to reach a run boundary
+
+// A decoded nonzero in shared memory: its value (compute type) and all N
+// indices; records are padded to a multiple of 16 bytes.
+template <int NT, typename C> struct __align__(16) Rec {
+    static constexpr int NI = NT ? NT : kMaxModes;
+    C val;
+    uint32_t idx[NI];
+};
+template <int NT, typename C> struct RecStride {
+    static constexpr int B = (int)((sizeof(Rec<NT, C>) + 15) / 16 * 16);
+};
+
+__device__ __forceinline__ uint32_t lane_lt_mask() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Open-addressing hash set of the hot rows in shared memory (row -> slot).
+constexpr int kHotHash = 2 * kHotMax;
+__device__ __forceinline__ uint32_t hot_hash(uint32_t row) { return (row * 2654435761u) >> 23; }  // 9 bits
+
+// Shared-memory bytes of the per-tile area: raw stage (words, values),
+// records, row counters, hot-row hash, mbarrier.
+template <int NT, int KW, typename C> constexpr size_t tile_bytes() {
+    return (size_t)kTile * (4 * KW) + (size_t)kTile * 8 + (size_t)kTile * RecStride<NT, C>::B +
+           (size_t)kSortBins * 4 + (size_t)kHotHash * 8 + 16;
+}
+
+// ---- TMA bulk copy (global -> shared) completing on an mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^22 polls (well over a second) and reports it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int NT, int KW, typename FT, int VEC, int VPL>
+__global__ void __launch_bounds__(kThreads, 2) k_mttkrp(const MttkrpArgs a, const int log2G) {
     using C = typename Prec<FT>::C;
     using Word = typename WordT<KW>::T;
+    using R_t = Rec<NT, C>;
+    constexpr int RB = RecStride<NT, C>::B;
+    constexpr int U = Unroll<FT, VPL>::U;
+    constexpr int NI = R_t::NI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sacc = reinterpret_cast<C *>(smem_raw);
 
     const int N = NT ? NT : a.N;
     const int G = 1 << log2G;
@@ -147,9 +222,25 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs a, const i
     const int mode = a.mode;
     const int mshift = a.fields.shift[mode];
     const uint32_t mmask = a.fields.mask[mode];
-    const VT *__restrict__ vals = reinterpret_cast<const VT *>(a.vals);
     C *__restrict__ out = reinterpret_cast<C *>(a.out);
     const int strat = a.strategy;
+    const bool priv = strat == RELATE_CONFLICT_PRIVATIZED;
+    const bool sort_tiles = strat != RELATE_CONFLICT_ATOMIC;
+    const int hot_n = priv ? 0 : a.hot_n;
+    const int vb = a.vals_f64 ? 8 : 4;
+
+    // shared layout: accumulators | raw words | raw values | records | hot slots | row counters | mbarrier
+    const int64_t acc_elems = priv ? (int64_t)a.In * R : (int64_t)hot_n * R;
+    C *sacc = reinterpret_cast<C *>(smem_raw);
+    unsigned char *tarea = smem_raw + ((acc_elems * (int64_t)sizeof(C) + 15) & ~(int64_t)15);
+    Word *sw = reinterpret_cast<Word *>(tarea);
+    unsigned char *sv = tarea + (size_t)kTile * sizeof(Word);
+    unsigned char *srec = sv + (size_t)kTile * 8;
+    uint32_t *bins = reinterpret_cast<uint32_t *>(srec + (size_t)kTile * RB);
+    uint32_t *hkey = bins + kSortBins;     // hot-row hash: keys (row ids)
+    uint32_t *hval = hkey + kHotHash;      // and their slots
+    uint64_t *bar = reinterpret_cast<uint64_t *>(hval + kHotHash);
+    __shared__ uint32_t wsum[kThreads / 32];
 
     int vj[VPL];
     bool act[VPL];
@@ -158,49 +249,196 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs a, const i
         vj[v] = gl + v * G;
         act[v] = vj[v] < nvec;
     }
-
-    if (strat == RELATE_CONFLICT_PRIVATIZED) {
-        const int64_t tot = (int64_t)a.In * R;
-        for (int64_t i = threadIdx.x; i < tot; i += kThreads) sacc[i] = C(0);
+    for (int64_t i = threadIdx.x; i < acc_elems; i += kThreads) sacc[i] = C(0);
+    if (hot_n) {  // hash set of this mode's hot rows (most populated first)
+        for (int i = threadIdx.x; i < kHotHash; i += kThreads) hkey[i] = 0xffffffffu;
         __syncthreads();
-    }
-
-    for (int64_t q = blockIdx.x; q < a.P; q += gridDim.x) {
-        const int64_t b = q * a.S;
-        const int64_t e = min(b + a.S, a.nnz);
-        const int64_t chunk = (e - b + ngroups - 1) / ngroups;
-        const int64_t jb = min(b + gid * chunk, e);
-        const int64_t je = min(jb + chunk, e);
-
-        bool win = false;
-        uint32_t wlo = 0, wrows = 0;
-        if (strat == RELATE_CONFLICT_SEGMENTED) {
-            wlo = a.plo[q * N + mode];
-            wrows = a.phi[q * N + mode] - wlo + 1;
-            win = (int)wrows <= a.window_rows;
-            if (win) {
-                const int tot = (int)wrows * R;
-                for (int i = threadIdx.x; i < tot; i += kThreads) sacc[i] = C(0);
-                __syncthreads();
+        for (int t = threadIdx.x; t < hot_n; t += kThreads) {
+            const uint32_t row = __ldg(a.hot_rows + t);
+            if (row == 0xffffffffu) continue;
+            uint32_t h = hot_hash(row);
+            for (int probe = 0; probe < kHotHash; probe++, h = (h + 1) & (kHotHash - 1)) {
+                const uint32_t prev = atomicCAS(hkey + h, 0xffffffffu, row);
+                if (prev == 0xffffffffu) {
+                    hval[h] = (uint32_t)t;
+                    break;
+                }
+                if (prev == row) break;
             }
         }
-        C *acc_base;          // where runs are flushed
-        int64_t row_bias;     // row offset subtracted before indexing acc_base
-        bool shared_acc;
-        if (strat == RELATE_CONFLICT_PRIVATIZED) {
-            acc_base = sacc;
-            row_bias = 0;
-            shared_acc = true;
-        } else if (win) {
-            acc_base = sacc;
-            row_bias = wlo;
-            shared_acc = true;
+        __syncthreads();
+    }
+    // slot of a hot row, or 0xffffffff: a few shared-memory probes
+    auto hot_slot_of = [&](uint32_t row) -> uint32_t {
+        uint32_t h = hot_hash(row);
+        for (int probe = 0; probe < kHotHash; probe++, h = (h + 1) & (kHotHash - 1)) {
+            const uint32_t k = hkey[h];
+            if (k == row) return hval[h];
+            if (k == 0xffffffffu) return 0xffffffffu;
+        }
+        return 0xffffffffu;
+    };
+
+    const int64_t tiles_per_part = (a.S + kTile - 1) / kTile;
+    const int64_t ntiles = a.P * tiles_per_part;
+    // TMA needs 16-byte aligned tile starts: partitions of a multiple of 4 nonzeros
+    const bool use_tma = (a.S % 4) == 0;
+    auto tile_span = [&](int64_t tq, int64_t &b, int &nt) {
+        const int64_t q = tq / tiles_per_part;
+        b = q * a.S + (tq - q * tiles_per_part) * kTile;
+        const int64_t pe = min(q * a.S + a.S, a.nnz);
+        nt = (int)max((int64_t)0, min((int64_t)kTile, pe - b));
+    };
+    auto issue = [&](int64_t tq) {  // one thread: stage tile tq through TMA
+        int64_t b;
+        int nt;
+        tile_span(tq, b, nt);
+        if (nt == 0) return;
+        const uint32_t wbytes = (uint32_t)((nt * sizeof(Word) + 15) & ~(size_t)15);
+        const uint32_t vbytes = (uint32_t)((nt * vb + 15) & ~15);
+        mbar_expect_tx(bar, wbytes + vbytes);
+        bulk_g2s(sw, reinterpret_cast<const Word *>(a.words) + b, wbytes, bar);
+        bulk_g2s(sv, reinterpret_cast<const unsigned char *>(a.vals) + b * vb, vbytes, bar);
+    };
+    if (use_tma) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && blockIdx.x < ntiles) issue(blockIdx.x);
+    }
+    uint32_t phase = 0;
+
+    for (int64_t tq = blockIdx.x; tq < ntiles; tq += gridDim.x) {
+        int64_t b;
+        int nt;
+        tile_span(tq, b, nt);
+        if (nt == 0) {  // uniform; no copy was issued for an empty tile, stage the next one
+            if (use_tma && threadIdx.x == 0 && tq + gridDim.x < ntiles) issue(tq + gridDim.x);
+            continue;
+        }
+        const int64_t q = tq / tiles_per_part;
+        if (use_tma) {
+            const bool ok = mbar_wait_bounded(bar, phase);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) {  // a copy never landed: report and stop
+                if (threadIdx.x == 0) atomicOr(a.err, 1);
+                return;
+            }
         } else {
-            acc_base = out;
-            row_bias = 0;
-            shared_acc = false;
+            __syncthreads();  // the previous tile is fully consumed
+            for (int j = threadIdx.x; j < nt; j += kThreads) {
+                sw[j] = load_word<KW>(a.words, b + j);
+                if (a.vals_f64)
+                    reinterpret_cast<double *>(sv)[j] = __ldg(reinterpret_cast<const double *>(a.vals) + b + j);
+                else
+                    reinterpret_cast<float *>(sv)[j] = __ldg(reinterpret_cast<const float *>(a.vals) + b + j);
+            }
+            __syncthreads();
         }
 
+        // ---- block-local counting sort of the tile by output row: bins are
+        // rows - lo when the partition's rows span at most kSortBins, else a
+        // 12-bit multiplicative hash of the row (equal rows share a bin, so
+        // their nonzeros stay adjacent unless another row hashes alike)
+        const uint32_t lo = a.plo[q * N + mode];
+        const uint32_t span = a.phi[q * N + mode] - lo + 1;
+        const bool direct = span <= (uint32_t)kSortBins;
+        const uint32_t nb = direct ? span : (uint32_t)kSortBins;
+        const bool sorted = sort_tiles;
+        auto bin_of = [&](uint32_t row) -> uint32_t { return direct ? row - lo : (row * 2654435761u) >> 20; };
+        if (sorted) {
+            for (uint32_t i = threadIdx.x; i < nb; i += kThreads) bins[i] = 0;
+            __syncthreads();
+#pragma unroll 4
+            for (int i = 0; i < kItems; i++) {
+                const int j = i * kThreads + threadIdx.x;
+                const uint32_t r = j < nt ? bin_of(fld(sw[j], mshift, mmask)) : 0xffffffffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, r);
+                if (r != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(bins + r, (uint32_t)__popc(peers));
+            }
+            __syncthreads();
+            {   // exclusive scan of the nb counters, a contiguous slice per thread
+                constexpr int PER = kSortBins / kThreads;
+                const int base = threadIdx.x * PER;
+                uint32_t loc[PER];
+                uint32_t sum = 0;
+#pragma unroll
+                for (int i = 0; i < PER; i++) {
+                    loc[i] = base + i < (int)nb ? bins[base + i] : 0u;
+                    sum += loc[i];
+                }
+                uint32_t incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (lane == 31) wsum[threadIdx.x >> 5] = incl;
+                __syncthreads();
+                uint32_t run = incl - sum;
+                for (int w = 0; w < (threadIdx.x >> 5); w++) run += wsum[w];
+#pragma unroll
+                for (int i = 0; i < PER; i++) {
+                    if (base + i < (int)nb) bins[base + i] = run;
+                    run += loc[i];
+                }
+            }
+            __syncthreads();
+        }
+        // ---- decode each nonzero once into its record at its (sorted) position
+#pragma unroll 4
+        for (int i = 0; i < kItems; i++) {
+            const int j = i * kThreads + threadIdx.x;
+            Word w{};
+            uint32_t row = 0xffffffffu;
+            if (j < nt) {
+                w = sw[j];
+                row = fld(w, mshift, mmask);
+            }
+            uint32_t p = (uint32_t)j;
+            if (sorted) {
+                const uint32_t r = row == 0xffffffffu ? 0xffffffffu : bin_of(row);
+                const uint32_t peers = __match_any_sync(0xffffffffu, r);
+                const int leader = __ffs(peers) - 1;
+                uint32_t p0 = 0;
+                if (r != 0xffffffffu && lane == leader) p0 = atomicAdd(bins + r, (uint32_t)__popc(peers));
+                p0 = __shfl_sync(0xffffffffu, p0, leader);
+                p = p0 + __popc(peers & lane_lt_mask());
+            }
+            if (j < nt) {
+                R_t rec;
+                rec.val = a.vals_f64 ? (C)reinterpret_cast<const double *>(sv)[j]
+                                     : (C)reinterpret_cast<const float *>(sv)[j];
+#pragma unroll
+                for (int k = 0; k < NI; k++) rec.idx[k] = k < N ? fld(w, a.rshift[k], a.rmask[k]) : 0u;
+                if (hot_n) {  // slot 0 becomes the run's destination: 0x80000000|slot for a hot row
+                    const uint32_t hs = hot_slot_of(row);
+                    if (hs != 0xffffffffu) rec.idx[0] = 0x80000000u | hs;
+                }
+                *reinterpret_cast<R_t *>(srec + (size_t)p * RB) = rec;
+            }
+        }
+        __syncthreads();  // records complete; the raw stage is free
+        if (use_tma && threadIdx.x == 0 && tq + gridDim.x < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(tq + gridDim.x);  // lands while this tile computes
+        }
+
+        // ---- each group walks a contiguous slice of the records; slice
+        // boundaries move forward to the next change of output row (at most
+        // kSnap records) so that short runs are not split between groups
+        const int chunk = (nt + ngroups - 1) / ngroups;
+        auto snap = [&](int x) -> int {  // monotone in x because chunk >= kSnap
+            if (x <= 0 || x >= nt || chunk < kSnap) return min(max(x, 0), nt);
+            const uint32_t prev = reinterpret_cast<const R_t *>(srec + (size_t)(x - 1) * RB)->idx[0];
+            for (int y = x; y < nt && y < x + kSnap; y++)
+                if (reinterpret_cast<const R_t *>(srec + (size_t)y * RB)->idx[0] != prev) return y;
+            return x;
+        };
+        const int jb = snap(gid * chunk);
+        const int je = snap((gid + 1) * chunk);
         uint32_t cur = 0xffffffffu;
         C acc[VPL][VEC];
 #pragma unroll
@@ -209,7 +447,16 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs a, const i
             for (int i = 0; i < VEC; i++) acc[v][i] = C(0);
 
         auto flush = [&](uint32_t row) {
-            C *dst = acc_base + ((int64_t)row - row_bias) * R;
+            C *dst;
+            bool shared_acc = true;
+            if (priv) {
+                dst = sacc + (int64_t)row * R;
+            } else if (row & 0x80000000u) {  // hot row: its shared-memory slot
+                dst = sacc + (int64_t)(row & 0x7fffffffu) * R;
+            } else {
+                dst = out + (int64_t)row * R;
+                shared_acc = false;
+            }
 #pragma unroll
             for (int v = 0; v < VPL; v++) {
                 if (!act[v]) continue;
@@ -217,127 +464,152 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs a, const i
                 if (shared_acc) {
 #pragma unroll
                     for (int i = 0; i < VEC; i++)
-                        if (vj[v] * VEC + i < R) atomicAdd(p + i, acc[v][i]);
+                        if (VEC == 1 || vj[v] * VEC + i < R) atomicAdd(p + i, acc[v][i]);
+                } else if (VEC == 1 || (vj[v] + 1) * VEC <= R) {
+                    GAdd<C, VEC>::run(p, acc[v]);
                 } else {
-                    if (VEC == 1 || (vj[v] + 1) * VEC <= R) {
-                        GAdd<C, VEC>::run(p, acc[v]);
-                    } else {
 #pragma unroll
-                        for (int i = 0; i < VEC; i++)
-                            if (vj[v] * VEC + i < R) atomicAdd(p + i, acc[v][i]);
-                    }
+                    for (int i = 0; i < VEC; i++)
+                        if (vj[v] * VEC + i < R) atomicAdd(p + i, acc[v][i]);
                 }
             }
         };
 
-        for (int64_t j = jb; j < je; j++) {
-            const Word w = load_word<KW>(a.words, j);
-            const C val = (C)__ldg(vals + j);
-            const uint32_t row = fld(w, mshift, mmask);
-            if (row != cur) {
-                if (cur != 0xffffffffu) flush(cur);
+        for (int p0 = jb; p0 < je; p0 += U) {
+            R_t rec[U];
+            C t[U][VPL][VEC];
 #pragma unroll
-                for (int v = 0; v < VPL; v++)
+            for (int u = 0; u < U; u++) rec[u] = *reinterpret_cast<const R_t *>(srec + (size_t)min(p0 + u, je - 1) * RB);
+            bool first = true;
 #pragma unroll
-                    for (int i = 0; i < VEC; i++) acc[v][i] = C(0);
-                cur = row;
+            for (int k = 1; k < NI; k++) {  // record slots 1..N-1: the other modes
+                if (k >= N) continue;
+                const FT *__restrict__ Ak = reinterpret_cast<const FT *>(a.rfac[k]);
+                C x[U][VPL][VEC];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const FT *rowp = Ak + (int64_t)rec[u].idx[k] * R;
+#pragma unroll
+                    for (int v = 0; v < VPL; v++)
+                        if (act[v]) VecLoad<FT, VEC>::run(rowp, vj[v], x[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++)
+#pragma unroll
+                    for (int v = 0; v < VPL; v++)
+#pragma unroll
+                        for (int i = 0; i < VEC; i++) t[u][v][i] = first ? x[u][v][i] : t[u][v][i] * x[u][v][i];
+                first = false;
             }
-            C t[VPL][VEC];
+            if (first) {  // one-mode tensor slice (N == 1 never happens; keeps t defined)
 #pragma unroll
-            for (int v = 0; v < VPL; v++)
+                for (int u = 0; u < U; u++)
 #pragma unroll
-                for (int i = 0; i < VEC; i++) t[v][i] = val;
+                    for (int v = 0; v < VPL; v++)
 #pragma unroll
-            for (int k = 0; k < (NT ? NT : kMaxModes); k++) {
-                if (k >= N || k == mode) continue;
-                const uint32_t ik = fld(w, a.fields.shift[k], a.fields.mask[k]);
-                const FT *rowp = reinterpret_cast<const FT *>(a.factors[k]) + (int64_t)ik * R;
+                        for (int i = 0; i < VEC; i++) t[u][v][i] = C(1);
+            }
 #pragma unroll
-                for (int v = 0; v < VPL; v++) {
-                    if (!act[v]) continue;
-                    C x[VEC];
-                    VecLoad<FT, VEC>::run(rowp, vj[v], x);
+            for (int u = 0; u < U; u++) {
+                if (p0 + u >= je) continue;
+                const uint32_t row = rec[u].idx[0];
+                const C val = rec[u].val;
+                if (row != cur) {
+                    if (cur != 0xffffffffu) flush(cur);
+                    cur = row;
 #pragma unroll
-                    for (int i = 0; i < VEC; i++) t[v][i] *= x[i];
+                    for (int v = 0; v < VPL; v++)
+#pragma unroll
+                        for (int i = 0; i < VEC; i++) acc[v][i] = val * t[u][v][i];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VPL; v++)
+#pragma unroll
+                        for (int i = 0; i < VEC; i++) acc[v][i] = fma(val, t[u][v][i], acc[v][i]);
                 }
             }
-#pragma unroll
-            for (int v = 0; v < VPL; v++)
-#pragma unroll
-                for (int i = 0; i < VEC; i++) acc[v][i] += t[v][i];
         }
         if (cur != 0xffffffffu) flush(cur);
-
-        if (win) {
-            __syncthreads();
-            const int tot = (int)wrows * R;
-            C *gdst = out + (int64_t)wlo * R;
-            for (int i = threadIdx.x; i < tot; i += kThreads) {
-                C s = sacc[i];
-                if (s != C(0)) atomicAdd(gdst + i, s);
-            }
-            __syncthreads();
-        } else if (strat == RELATE_CONFLICT_SEGMENTED) {
-            // keep the block's partitions in lock-step (a later partition may
-            // take the window path and zero the shared buffer)
-            __syncthreads();
-        }
     }
 
-    if (strat == RELATE_CONFLICT_PRIVATIZED) {
-        __syncthreads();
+    __syncthreads();
+    if (priv) {
         const int64_t tot = (int64_t)a.In * R;
         for (int64_t i = threadIdx.x; i < tot; i += kThreads) {
             C s = sacc[i];
             if (s != C(0)) atomicAdd(out + i, s);
         }
+    } else if (hot_n) {
+        const int tot = hot_n * R;
+        for (int i = threadIdx.x; i < tot; i += kThreads) {
+            const C s = sacc[i];
+            const uint32_t row = __ldg(a.hot_rows + i / R);
+            if (s != C(0) && row != 0xffffffffu) atomicAdd(out + (int64_t)row * R + i % R, s);
+        }
     }
 }
 
 // Chooses lanes per group for R and launches one instantiation.
-template <int NT, int KW, typename FT, typename VT, int VEC, int VPL>
-cudaError_t launch_one(const MttkrpArgs &a, size_t smem, int grid, cudaStream_t st) {
+template <int NT, int KW, typename FT, int VEC, int VPL>
+cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStream_t st) {
     const int nvec = (a.R + VEC - 1) / VEC;
     int G = 1, log2G = 0;
     while (G * VPL < nvec && G < 32) {
         G <<= 1;
         log2G++;
     }
-    auto kern = k_mttkrp<NT, KW, FT, VT, VEC, VPL>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const size_t smem = ((acc_bytes + 15) & ~(size_t)15) + tile_bytes<NT, KW, typename Prec<FT>::C>();
+    auto kern = k_mttkrp<NT, KW, FT, VEC, VPL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, smem, st>>>(a, log2G);
     return cudaGetLastError();
 }
 
-// Dispatch over N (3, 4, generic), word width and value dtype for one FT.
+// Dispatch over N (2..5 specialised, 6..8 generic) and word width for one FT.
 template <typename FT>
-cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, int val_dtype, bool vec_ok, size_t smem, int grid,
-                        cudaStream_t st) {
+cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st) {
     constexpr int V = Prec<FT>::VEC;
-#define RELATE_MK_VT(NT_, KW_, VT_)                                                    \
-    (vec_ok ? launch_one<NT_, KW_, FT, VT_, V, 1>(a, smem, grid, st)                   \
-            : launch_one<0, KW_, FT, VT_, 1, 2>(a, smem, grid, st))
-#define RELATE_MK_KW(NT_, VT_)                                                         \
-    (KW == 1 ? RELATE_MK_VT(NT_, 1, VT_) : KW == 2 ? RELATE_MK_VT(NT_, 2, VT_) : RELATE_MK_VT(NT_, 4, VT_))
-    if (val_dtype == RELATE_F64) {
-        if (a.N == 3) return RELATE_MK_KW(3, double);
-        if (a.N == 4) return RELATE_MK_KW(4, double);
-        return RELATE_MK_KW(0, double);
+#define RELATE_MK_KW(NT_)                                                                        \
+    (KW == 1 ? launch_one<NT_, 1, FT, V, 1>(a, acc_bytes, grid, st)                              \
+             : KW == 2 ? launch_one<NT_, 2, FT, V, 1>(a, acc_bytes, grid, st)                    \
+                       : launch_one<NT_, 4, FT, V, 1>(a, acc_bytes, grid, st))
+    if (!vec_ok) {
+        return KW == 1 ? launch_one<0, 1, FT, 1, 2>(a, acc_bytes, grid, st)
+                       : KW == 2 ? launch_one<0, 2, FT, 1, 2>(a, acc_bytes, grid, st)
+                                 : launch_one<0, 4, FT, 1, 2>(a, acc_bytes, grid, st);
     }
-    if (a.N == 3) return RELATE_MK_KW(3, float);
-    if (a.N == 4) return RELATE_MK_KW(4, float);
-    return RELATE_MK_KW(0, float);
+    switch (a.N) {
+    case 2: return RELATE_MK_KW(2);
+    case 3: return RELATE_MK_KW(3);
+    case 4: return RELATE_MK_KW(4);
+    case 5: return RELATE_MK_KW(5);
+    default: return RELATE_MK_KW(0);
+    }
 #undef RELATE_MK_KW
-#undef RELATE_MK_VT
+}
+
+// Per-tile shared bytes of the instantiation a launch will use.
+template <int KW>
+inline size_t tile_bytes_kw(int NT, bool f64) {
+    switch (NT) {
+    case 2: return f64 ? tile_bytes<2, KW, double>() : tile_bytes<2, KW, float>();
+    case 3: return f64 ? tile_bytes<3, KW, double>() : tile_bytes<3, KW, float>();
+    case 4: return f64 ? tile_bytes<4, KW, double>() : tile_bytes<4, KW, float>();
+    case 5: return f64 ? tile_bytes<5, KW, double>() : tile_bytes<5, KW, float>();
+    default: return f64 ? tile_bytes<0, KW, double>() : tile_bytes<0, KW, float>();
+    }
+}
+inline size_t tile_bytes_for(int N, int KW, int factor_dtype, bool vec_ok) {
+    const bool f64 = factor_dtype == RELATE_F64;
+    const int NT = (vec_ok && N >= 2 && N <= 5) ? N : 0;
+    return KW == 1 ? tile_bytes_kw<1>(NT, f64) : KW == 2 ? tile_bytes_kw<2>(NT, f64) : tile_bytes_kw<4>(NT, f64);
 }
 
 }  // namespace mk
 
-cudaError_t mttkrp_f64(const MttkrpArgs &a, int KW, int val_dtype, bool vec_ok, size_t smem, int grid, cudaStream_t st);
-cudaError_t mttkrp_f32(const MttkrpArgs &a, int KW, int val_dtype, bool vec_ok, size_t smem, int grid, cudaStream_t st);
-cudaError_t mttkrp_bf16(const MttkrpArgs &a, int KW, int val_dtype, bool vec_ok, size_t smem, int grid, cudaStream_t st);
+cudaError_t mttkrp_f64(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st);
+cudaError_t mttkrp_f32(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st);
+cudaError_t mttkrp_bf16(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st);
 
 }  // namespace relate

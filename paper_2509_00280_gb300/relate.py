@@ -81,6 +81,7 @@ def lib():
                 "relate_decode": (I, [P, P, P, P, P, P]),
                 "relate_get_partitions": (I, [P, P, P, P]),
                 "relate_gram": (I, [P, I64, I, I, P, P]),
+                "relate_sync_status": (I, [P, P]),
                 "relate_free": (None, [P]),
                 "relate_status_string": (ctypes.c_char_p, [I]),
                 "relate_last_error": (ctypes.c_char_p, []),
@@ -273,6 +274,10 @@ def relate_get_partitions(h: Handle, lo, hi, stream=None) -> None:
 def relate_gram(A, R: int, dtype, G, stream=None) -> None:
     I = int(A.shape[0]) if A is not None else 0
     _check(lib().relate_gram(_ptr(A), I, int(R), _DTYPES[dtype], _ptr(G), _stream(stream)), "relate_gram")
+
+
+def relate_sync_status(h: Handle, stream=None) -> None:
+    _check(lib().relate_sync_status(h.raw, _stream(stream)), "relate_sync_status")
 
 
 def relate_free(h: Handle) -> None:

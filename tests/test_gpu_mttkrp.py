@@ -50,6 +50,7 @@ def test_fp64_uniform_1M_all_modes(cfg_uniform, strategy):
     for n in range(3):
         got = mttkrp_dev(h, n, dfs, 16, acc="f64")
         assert rel_fro(got, refs[n]) <= 1e-12, (n, strategy)
+    rl.relate_sync_status(h)  # no bounded wait gave up
     h.close()
 
 
