@@ -38,7 +38,8 @@ __device__ __forceinline__ void pair_of(int p, int R, int &r, int &s) {
 }
 
 // Per-block partial of the upper triangle of A^T A. FP32/BF16 inputs
-// accumulate in FP32 within a 32-row tile and in FP64 across tiles.
+// accumulate in FP32 over the block's rows (at most a few thousand), FP64
+// inputs in FP64; blocks are combined in FP64.
 template <typename FT>
 __global__ void __launch_bounds__(kThreads) k_gram_partial(const FT *__restrict__ A, int64_t I, int R,
                                                            double *__restrict__ partial) {
@@ -46,13 +47,13 @@ __global__ void __launch_bounds__(kThreads) k_gram_partial(const FT *__restrict_
     __shared__ T tile[GR_ROWS][MAXR + 1];
     const int npairs = R * (R + 1) / 2;
     int pr[PAIRS_PER_THREAD], ps[PAIRS_PER_THREAD];
-    double acc[PAIRS_PER_THREAD];
+    T acc[PAIRS_PER_THREAD];
 #pragma unroll
     for (int u = 0; u < PAIRS_PER_THREAD; u++) {
         const int p = threadIdx.x + u * kThreads;
         pr[u] = ps[u] = 0;
         if (p < npairs) pair_of(p, R, pr[u], ps[u]);
-        acc[u] = 0.0;
+        acc[u] = T(0);
     }
     for (int64_t r0 = (int64_t)blockIdx.x * GR_ROWS; r0 < I; r0 += (int64_t)gridDim.x * GR_ROWS) {
         for (int idx = threadIdx.x; idx < GR_ROWS * R; idx += kThreads) {
@@ -64,10 +65,10 @@ __global__ void __launch_bounds__(kThreads) k_gram_partial(const FT *__restrict_
 #pragma unroll
         for (int u = 0; u < PAIRS_PER_THREAD; u++) {
             if (threadIdx.x + u * kThreads < npairs) {
-                T s = T(0);
+                T s = acc[u];
 #pragma unroll 8
                 for (int i = 0; i < GR_ROWS; i++) s = fma(tile[i][pr[u]], tile[i][ps[u]], s);
-                acc[u] += (double)s;
+                acc[u] = s;
             }
         }
         __syncthreads();
@@ -75,30 +76,47 @@ __global__ void __launch_bounds__(kThreads) k_gram_partial(const FT *__restrict_
 #pragma unroll
     for (int u = 0; u < PAIRS_PER_THREAD; u++) {
         const int p = threadIdx.x + u * kThreads;
-        if (p < npairs) partial[(int64_t)blockIdx.x * npairs + p] = acc[u];
+        if (p < npairs) partial[(int64_t)blockIdx.x * npairs + p] = (double)acc[u];
     }
+}
+
+// Deterministic warp sum: lane l adds partials l, l+32, ... in order, then a
+// fixed xor tree combines the lanes.
+__device__ __forceinline__ double warp_sum_strided(const double *__restrict__ base, int n, int stride) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < n; b += 32) s += base[(int64_t)b * stride];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
 }
 
 __global__ void __launch_bounds__(kThreads) k_gram_reduce(const double *__restrict__ partial, int nblocks, int R,
                                                           double *__restrict__ G) {
     const int npairs = R * (R + 1) / 2;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; b++) s += partial[(int64_t)b * npairs + p];
-        int r, c;
-        pair_of(p, R, r, c);
-        G[r * R + c] = s;
-        G[c * R + r] = s;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int p = warp; p < npairs; p += nwarps) {
+        const double s = warp_sum_strided(partial + p, nblocks, npairs);
+        if ((threadIdx.x & 31) == 0) {
+            int r, c;
+            pair_of(p, R, r, c);
+            G[r * R + c] = s;
+            G[c * R + r] = s;
+        }
     }
 }
 
 // V = Hadamard_{k != n} G_k, Cholesky (FP64, one ridge retry), V^{-1}.
+// FP64 on GB300 is a narrow pipe, so the factorisation keeps its serial
+// chains short: one square root and one reciprocal per column, the column
+// scaling and the trailing update spread over the block.
 __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict__ G_all, int N, int n, int R,
                                                         double *__restrict__ Vinv, float *__restrict__ Vinv32,
                                                         int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double(*L)[MAXR + 1] = reinterpret_cast<double(*)[MAXR + 1]>(smem_raw);
     double(*Li)[MAXR + 1] = reinterpret_cast<double(*)[MAXR + 1]>(smem_raw + sizeof(double) * MAXR * (MAXR + 1));
+    __shared__ double rdiag[MAXR];
     __shared__ int fail;
     __shared__ double ridge;
     const int RR = R * R;
@@ -110,12 +128,13 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
             L[idx / R][idx % R] = v;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            fail = 0;
-            if (attempt == 0) {
-                double tr = 0.0;
-                for (int r = 0; r < R; r++) tr += L[r][r];
-                ridge = 1e-12 * tr / R;
+        if (threadIdx.x < 32) {
+            double tr = 0.0;
+            for (int r = threadIdx.x; r < R; r += 32) tr += L[r][r];
+            for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+            if (threadIdx.x == 0) {
+                fail = 0;
+                if (attempt == 0) ridge = 1e-12 * tr / R;
             }
         }
         __syncthreads();
@@ -123,21 +142,25 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
             for (int r = threadIdx.x; r < R; r += kThreads) L[r][r] += ridge;
         __syncthreads();
         for (int j = 0; j < R; j++) {
-            if (threadIdx.x == 0) {
-                const double d = L[j][j];
-                if (!(d > 0.0))
-                    fail = 1;
-                else
-                    L[j][j] = sqrt(d);
+            // every thread reads the pivot (no serial section)
+            const double d = L[j][j];
+            if (!(d > 0.0)) {
+                if (threadIdx.x == 0) fail = 1;
+                break;
             }
-            __syncthreads();
-            if (fail) break;
-            for (int i = j + 1 + threadIdx.x; i < R; i += kThreads) L[i][j] /= L[j][j];
+            const double ljj = sqrt(d);
+            const double inv = 1.0 / ljj;
+            __syncthreads();  // all threads have read L[j][j]
+            if (threadIdx.x == 0) {
+                L[j][j] = ljj;
+                rdiag[j] = inv;
+            }
+            for (int i = j + 1 + threadIdx.x; i < R; i += kThreads) L[i][j] *= inv;
             __syncthreads();
             const int m = R - j - 1;
             for (int t = threadIdx.x; t < m * m; t += kThreads) {
                 const int i = j + 1 + t / m, k = j + 1 + t % m;
-                if (k <= i) L[i][k] -= L[i][j] * L[k][j];
+                if (k <= i) L[i][k] = fma(-L[i][j], L[k][j], L[i][k]);
             }
             __syncthreads();
         }
@@ -157,11 +180,11 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
     // L^{-1} column by column (forward substitution on unit vectors)
     for (int c = threadIdx.x; c < R; c += kThreads) {
         for (int i = 0; i < c; i++) Li[i][c] = 0.0;
-        Li[c][c] = 1.0 / L[c][c];
+        Li[c][c] = rdiag[c];
         for (int i = c + 1; i < R; i++) {
             double s = 0.0;
-            for (int k = c; k < i; k++) s += L[i][k] * Li[k][c];
-            Li[i][c] = -s / L[i][i];
+            for (int k = c; k < i; k++) s = fma(L[i][k], Li[k][c], s);
+            Li[i][c] = -s * rdiag[i];
         }
     }
     __syncthreads();
@@ -169,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
     for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
         const int i = idx / R, j = idx % R;
         double s = 0.0;
-        for (int k = max(i, j); k < R; k++) s += Li[k][i] * Li[k][j];
+        for (int k = max(i, j); k < R; k++) s = fma(Li[k][i], Li[k][j], s);
         Vinv[idx] = s;
         Vinv32[idx] = (float)s;
     }
@@ -186,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_solve_rows(C *__restrict__ M, int6
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c0 = lane, c1 = lane + 32;
-    double d0 = 0.0, d1 = 0.0;
+    C d0 = C(0), d1 = C(0);  // this warp's share of <M_old(:,c), M_new(:,c)>
     for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + warp; i < I; i += (int64_t)gridDim.x * (kThreads / 32)) {
         C *row = M + i * R;
         const C x0 = c0 < R ? row[c0] : C(0);
@@ -199,15 +222,15 @@ __global__ void __launch_bounds__(kThreads) k_solve_rows(C *__restrict__ M, int6
         }
         if (c0 < R) {
             row[c0] = y0;
-            d0 += (double)x0 * (double)y0;
+            d0 = fma(x0, y0, d0);
         }
         if (c1 < R) {
             row[c1] = y1;
-            d1 += (double)x1 * (double)y1;
+            d1 = fma(x1, y1, d1);
         }
     }
-    red[warp][c0] = d0;
-    red[warp][c1] = d1;
+    red[warp][c0] = (double)d0;
+    red[warp][c1] = (double)d1;
     __syncthreads();
     for (int c = threadIdx.x; c < R; c += kThreads) {
         double s = 0.0;
@@ -221,13 +244,15 @@ __global__ void __launch_bounds__(kThreads) k_finish_mode(const double *__restri
                                                           double *__restrict__ lambda, double *__restrict__ G,
                                                           double *__restrict__ inner) {
     __shared__ double lam[MAXR];
-    for (int r = threadIdx.x; r < R; r += kThreads) {
-        const double l = sqrt(G[r * R + r]);
-        lam[r] = l;
-        lambda[r] = l;
-        double s = 0.0;
-        for (int b = 0; b < nblocks; b++) s += partial[(int64_t)b * MAXR + r];
-        inner[r] = l > 0.0 ? s / l : 0.0;
+    const int warp = threadIdx.x >> 5;
+    for (int r = warp; r < R; r += kThreads / 32) {
+        const double s = warp_sum_strided(partial + r, nblocks, MAXR);
+        if ((threadIdx.x & 31) == 0) {
+            const double l = sqrt(G[r * R + r]);
+            lam[r] = l;
+            lambda[r] = l;
+            inner[r] = l > 0.0 ? s / l : 0.0;
+        }
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < R * R; idx += kThreads) {
@@ -306,7 +331,7 @@ cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scra
     default: k_gram_partial<__nv_bfloat16><<<g, kThreads, 0, st>>>((const __nv_bfloat16 *)A, I, R, scratch); break;
     }
     const int npairs = R * (R + 1) / 2;
-    k_gram_reduce<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, st>>>(scratch, g, R, G);
+    k_gram_reduce<<<(npairs + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(scratch, g, R, G);
     return cudaGetLastError();
 }
 
