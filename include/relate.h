@@ -210,6 +210,23 @@ int relate_get_partitions(relate_handle_t h, uint32_t *lo, uint32_t *hi, void *s
  * within blocks of rows and in FP64 across blocks. Async on stream. */
 int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream);
 
+/* The same Gram step as relate_gram, for callers that cannot allocate device
+ * memory when they call it (e.g. inside a host callback enqueued on a stream,
+ * or with all device memory already handed to their own pool): the per-block
+ * partial sums live in a fixed 5.06 MB array compiled into the library
+ * instead of a per-call allocation. The paper has no counterpart; this is a
+ * deployment variant of the Gram step of CP-ALS.
+ * A, G, R, dtype, stream: as for relate_gram (A DEVICE I x R row-major, G
+ * DEVICE R x R FP64). R outside [1, 64] is rejected (RELATE_ERR_INVALID_ARG)
+ * because the array holds the partials of at most 64 columns.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before capturing
+ * any stream work. Calls on one device share the array, so calls whose
+ * kernels may overlap on the GPU (unordered streams) race and must be
+ * serialised by the caller. Nothing needs clearing between calls: each call
+ * writes every partial it reads. Allocates nothing; asynchronous on stream. */
+int relate_gram_noalloc(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream);
+
 /* Synchronises `stream` and reports whether any kernel of this handle gave
  * up a bounded device wait since the last call (RELATE_ERR_TIMEOUT; the flag
  * is then cleared). The MTTKRP kernel waits on its own tile copies with an

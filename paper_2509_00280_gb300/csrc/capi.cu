@@ -37,6 +37,15 @@ int dtype_bytes(int d) { return d == RELATE_F64 ? 8 : d == RELATE_F32 ? 4 : 2; }
 
 }  // namespace
 
+namespace relate {
+// Records the last-error message of this host thread for entry points in other
+// translation units; returns status.
+int set_last_error(int status, const char *msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg ? msg : "");
+    return status;
+}
+}  // namespace relate
+
 struct relate_handle_s {
     int N = 0;
     int64_t nnz = 0;

@@ -81,6 +81,7 @@ def lib():
                 "relate_decode": (I, [P, P, P, P, P, P]),
                 "relate_get_partitions": (I, [P, P, P, P]),
                 "relate_gram": (I, [P, I64, I, I, P, P]),
+                "relate_gram_noalloc": (I, [P, I64, I, I, P, P]),
                 "relate_sync_status": (I, [P, P]),
                 "relate_free": (None, [P]),
                 "relate_status_string": (ctypes.c_char_p, [I]),
@@ -278,6 +279,13 @@ def relate_gram(A, R: int, dtype, G, stream=None) -> None:
 
 def relate_sync_status(h: Handle, stream=None) -> None:
     _check(lib().relate_sync_status(h.raw, _stream(stream)), "relate_sync_status")
+
+
+def relate_gram_noalloc(A, R: int, dtype, G, stream=None) -> None:
+    """Gram step with the library's fixed scratch (no device allocation)."""
+    I = int(A.shape[0]) if A is not None else 0
+    _check(lib().relate_gram_noalloc(_ptr(A), I, int(R), _DTYPES[dtype], _ptr(G), _stream(stream)),
+           "relate_gram_noalloc")
 
 
 def relate_free(h: Handle) -> None:
