@@ -39,7 +39,9 @@ CPU_SAMPLE_NNZ = 5_000_000  # nonzeros of the workload the CPU oracle runs per s
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": None, "bytes_per_launch": None, "workload": None}
+NCU_TRAFFIC = {"sha256": "b942ea4c99b235fefe88b6d6f007041870d66bbcc457d41e649c84716381422e",
+               # 20M-nonzero capture, stream part scaled to 50M nonzeros
+               "bytes_per_launch": 655.9e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
 
 
 def _peaks():
