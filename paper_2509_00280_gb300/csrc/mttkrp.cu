@@ -38,7 +38,7 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
             a.rfac[j] = nullptr;
         }
     }
-    const size_t tile = mk::tile_bytes_for(a.N, KW, factor_dtype, vec_ok);
+    const size_t tile = mk::tile_bytes_for(a.N, KW, factor_dtype, vec_ok, a.vals_f64 ? 8 : 4);
     size_t acc_bytes = 0;
     if (a.strategy == RELATE_CONFLICT_PRIVATIZED && (size_t)a.In * a.R * accb + 16 + tile > (size_t)smem_budget)
         a.strategy = RELATE_CONFLICT_SEGMENTED;  // the whole output does not fit: sort tiles instead

@@ -136,7 +136,9 @@ template <int VPL> struct Unroll<__nv_bfloat16, VPL> { static constexpr int U = 
 
 constexpr int kTile = 2048;       // nonzeros per tile
 constexpr int kItems = kTile / kThreads;
-constexpr int kSortBins = 4096;   // widest row range a tile may span to be sorted
+constexpr int kSortBins = 2048;   // widest row range a tile may span to be sorted
+constexpr int kSortBinBits = 11;  // log2(kSortBins): hashed bins take this many bits
+static_assert((1 << kSortBinBits) == kSortBins, "sort bins must be a power of two");
 constexpr int kSnap = 16;         // records a slice boundary may move to reach a run boundary
 
 // A decoded nonzero in shared memory: its value (compute type) and all N
@@ -160,10 +162,10 @@ __device__ __forceinline__ uint32_t lane_lt_mask() {
 constexpr int kHotHash = 2 * kHotMax;
 __device__ __forceinline__ uint32_t hot_hash(uint32_t row) { return (row * 2654435761u) >> 23; }  // 9 bits
 
-// Shared-memory bytes of the per-tile area: raw stage (words, values),
-// records, row counters, hot-row hash, mbarrier.
-template <int NT, int KW, typename C> constexpr size_t tile_bytes() {
-    return (size_t)kTile * (4 * KW) + (size_t)kTile * 8 + (size_t)kTile * RecStride<NT, C>::B +
+// Shared-memory bytes of the per-tile area: raw stage (words, values of vb
+// bytes), records, row counters, hot-row hash, mbarrier.
+template <int NT, int KW, typename C> constexpr size_t tile_bytes(int vb) {
+    return (size_t)kTile * (4 * KW) + (size_t)kTile * vb + (size_t)kTile * RecStride<NT, C>::B +
            (size_t)kSortBins * 4 + (size_t)kHotHash * 8 + 16;
 }
 
@@ -202,7 +204,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 template <int NT, int KW, typename FT, int VEC, int VPL>
-__global__ void __launch_bounds__(kThreads, 2) k_mttkrp(const MttkrpArgs a, const int log2G) {
+__global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, const int log2G) {
     using C = typename Prec<FT>::C;
     using Word = typename WordT<KW>::T;
     using R_t = Rec<NT, C>;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mttkrp(const MttkrpArgs a, cons
     unsigned char *tarea = smem_raw + ((acc_elems * (int64_t)sizeof(C) + 15) & ~(int64_t)15);
     Word *sw = reinterpret_cast<Word *>(tarea);
     unsigned char *sv = tarea + (size_t)kTile * sizeof(Word);
-    unsigned char *srec = sv + (size_t)kTile * 8;
+    unsigned char *srec = sv + (size_t)kTile * vb;
     uint32_t *bins = reinterpret_cast<uint32_t *>(srec + (size_t)kTile * RB);
     uint32_t *hkey = bins + kSortBins;     // hot-row hash: keys (row ids)
     uint32_t *hval = hkey + kHotHash;      // and their slots
@@ -347,7 +349,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_mttkrp(const MttkrpArgs a, cons
         const bool direct = span <= (uint32_t)kSortBins;
         const uint32_t nb = direct ? span : (uint32_t)kSortBins;
         const bool sorted = sort_tiles;
-        auto bin_of = [&](uint32_t row) -> uint32_t { return direct ? row - lo : (row * 2654435761u) >> 20; };
+        auto bin_of = [&](uint32_t row) -> uint32_t {
+            return direct ? row - lo : (row * 2654435761u) >> (32 - kSortBinBits);
+        };
         if (sorted) {
             for (uint32_t i = threadIdx.x; i < nb; i += kThreads) bins[i] = 0;
             __syncthreads();
@@ -558,7 +562,7 @@ cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStre
         G <<= 1;
         log2G++;
     }
-    const size_t smem = ((acc_bytes + 15) & ~(size_t)15) + tile_bytes<NT, KW, typename Prec<FT>::C>();
+    const size_t smem = ((acc_bytes + 15) & ~(size_t)15) + tile_bytes<NT, KW, typename Prec<FT>::C>(a.vals_f64 ? 8 : 4);
     auto kern = k_mttkrp<NT, KW, FT, VEC, VPL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -591,19 +595,20 @@ cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_byt
 
 // Per-tile shared bytes of the instantiation a launch will use.
 template <int KW>
-inline size_t tile_bytes_kw(int NT, bool f64) {
+inline size_t tile_bytes_kw(int NT, bool f64, int vb) {
     switch (NT) {
-    case 2: return f64 ? tile_bytes<2, KW, double>() : tile_bytes<2, KW, float>();
-    case 3: return f64 ? tile_bytes<3, KW, double>() : tile_bytes<3, KW, float>();
-    case 4: return f64 ? tile_bytes<4, KW, double>() : tile_bytes<4, KW, float>();
-    case 5: return f64 ? tile_bytes<5, KW, double>() : tile_bytes<5, KW, float>();
-    default: return f64 ? tile_bytes<0, KW, double>() : tile_bytes<0, KW, float>();
+    case 2: return f64 ? tile_bytes<2, KW, double>(vb) : tile_bytes<2, KW, float>(vb);
+    case 3: return f64 ? tile_bytes<3, KW, double>(vb) : tile_bytes<3, KW, float>(vb);
+    case 4: return f64 ? tile_bytes<4, KW, double>(vb) : tile_bytes<4, KW, float>(vb);
+    case 5: return f64 ? tile_bytes<5, KW, double>(vb) : tile_bytes<5, KW, float>(vb);
+    default: return f64 ? tile_bytes<0, KW, double>(vb) : tile_bytes<0, KW, float>(vb);
     }
 }
-inline size_t tile_bytes_for(int N, int KW, int factor_dtype, bool vec_ok) {
+inline size_t tile_bytes_for(int N, int KW, int factor_dtype, bool vec_ok, int vb) {
     const bool f64 = factor_dtype == RELATE_F64;
     const int NT = (vec_ok && N >= 2 && N <= 5) ? N : 0;
-    return KW == 1 ? tile_bytes_kw<1>(NT, f64) : KW == 2 ? tile_bytes_kw<2>(NT, f64) : tile_bytes_kw<4>(NT, f64);
+    return KW == 1 ? tile_bytes_kw<1>(NT, f64, vb) : KW == 2 ? tile_bytes_kw<2>(NT, f64, vb)
+                                                            : tile_bytes_kw<4>(NT, f64, vb);
 }
 
 }  // namespace mk
