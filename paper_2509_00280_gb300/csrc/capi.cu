@@ -76,7 +76,7 @@ struct relate_handle_s {
     int ws_R = 0;
     void *d_M = nullptr;
     double *d_scratch = nullptr, *d_G = nullptr, *d_Vinv = nullptr, *d_lambda = nullptr, *d_inner = nullptr,
-           *d_fit = nullptr;
+           *d_fit = nullptr, *d_V = nullptr;
     float *d_Vinv32 = nullptr;
     int *d_status = nullptr;
 
@@ -84,7 +84,7 @@ struct relate_handle_s {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
         void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_err, d_M, d_scratch, d_G, d_Vinv,
-                        d_lambda, d_inner, d_fit, d_Vinv32, d_status};
+                        d_lambda, d_inner, d_fit, d_Vinv32, d_status, d_V};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         for (auto *p : d_counts)
@@ -173,12 +173,12 @@ struct AsyncBufs {
 int ensure_ws(relate_handle_s *h, int R) {
     if (h->ws_R >= R && h->d_M) return RELATE_OK;
     void *ptrs[] = {h->d_M, h->d_scratch, h->d_G, h->d_Vinv, h->d_lambda, h->d_inner, h->d_fit, h->d_Vinv32,
-                    h->d_status};
+                    h->d_status, h->d_V};
     cudaStreamSynchronize(h->stream);
     for (void *p : ptrs)
         if (p) cudaFree(p);
     h->d_M = nullptr;
-    h->d_scratch = h->d_G = h->d_Vinv = h->d_lambda = h->d_inner = h->d_fit = nullptr;
+    h->d_scratch = h->d_G = h->d_Vinv = h->d_lambda = h->d_inner = h->d_fit = h->d_V = nullptr;
     h->d_Vinv32 = nullptr;
     h->d_status = nullptr;
     h->ws_R = 0;
@@ -190,6 +190,7 @@ int ensure_ws(relate_handle_s *h, int R) {
         (e = cudaMalloc((void **)&h->d_scratch, dense_scratch_doubles(RM) * 8)) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_G, (size_t)h->N * RM * RM * 8)) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_Vinv, RM * RM * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_V, RM * RM * 8)) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_Vinv32, RM * RM * 4)) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_lambda, RM * 8)) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_inner, RM * 8)) != cudaSuccess ||
@@ -541,12 +542,11 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
             const int64_t In = (int64_t)h->dims[n];
             rc = run_mttkrp(h, n, factors, R, h->d_M, st);
             if (rc) return rc;
-            if ((e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_status, st)) != cudaSuccess ||
-                (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_scratch, st)) !=
-                    cudaSuccess ||
+            if ((e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
+                                      h->d_status, st)) != cudaSuccess ||
+                (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess ||
                 (e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) != cudaSuccess ||
-                (e = launch_finish_mode(h->d_scratch, In, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) !=
-                    cudaSuccess ||
+                (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess ||
                 (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype, st)) !=
                     cudaSuccess)
                 return cuda_fail(e, "relate_cpals: mode update");

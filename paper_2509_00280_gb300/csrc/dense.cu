@@ -55,13 +55,27 @@ __global__ void __launch_bounds__(kThreads) k_gram_partial(const FT *__restrict_
         if (p < npairs) pair_of(p, R, pr[u], ps[u]);
         acc[u] = T(0);
     }
-    for (int64_t r0 = (int64_t)blockIdx.x * GR_ROWS; r0 < I; r0 += (int64_t)gridDim.x * GR_ROWS) {
-        for (int idx = threadIdx.x; idx < GR_ROWS * R; idx += kThreads) {
+    // the next tile's elements are loaded into registers while this one computes
+    constexpr int LD = (GR_ROWS * MAXR + kThreads - 1) / kThreads;
+    T pre[LD];
+    auto fetch = [&](int64_t r0) {
+#pragma unroll
+        for (int u = 0; u < LD; u++) {
+            const int idx = threadIdx.x + u * kThreads;
             const int i = idx / R, c = idx - i * R;
             const int64_t row = r0 + i;
-            tile[i][c] = row < I ? ld_as<FT>(A + row * R + c) : T(0);
+            pre[u] = (idx < GR_ROWS * R && row < I) ? ld_as<FT>(A + row * R + c) : T(0);
+        }
+    };
+    fetch((int64_t)blockIdx.x * GR_ROWS);
+    for (int64_t r0 = (int64_t)blockIdx.x * GR_ROWS; r0 < I; r0 += (int64_t)gridDim.x * GR_ROWS) {
+#pragma unroll
+        for (int u = 0; u < LD; u++) {
+            const int idx = threadIdx.x + u * kThreads;
+            if (idx < GR_ROWS * R) tile[idx / R][idx % R] = pre[u];
         }
         __syncthreads();
+        fetch(r0 + (int64_t)gridDim.x * GR_ROWS);
 #pragma unroll
         for (int u = 0; u < PAIRS_PER_THREAD; u++) {
             if (threadIdx.x + u * kThreads < npairs) {
@@ -107,11 +121,14 @@ __global__ void __launch_bounds__(kThreads) k_gram_reduce(const double *__restri
 }
 
 // V = Hadamard_{k != n} G_k, Cholesky (FP64, one ridge retry), V^{-1}.
-// FP64 on GB300 is a narrow pipe, so the factorisation keeps its serial
-// chains short: one square root and one reciprocal per column, the column
-// scaling and the trailing update spread over the block.
+// FP64 is a narrow pipe on GB300: square roots and reciprocals are computed
+// once per column by one thread, the O(R^3) parts are spread over the block,
+// and for FP32 / BF16 factors V^{-1} = L^{-T} L^{-1} is formed in FP32 from
+// the FP64 L^{-1} (it is applied in FP32). V itself is kept (Vsave) for the
+// fit's inner products.
 __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict__ G_all, int N, int n, int R,
                                                         double *__restrict__ Vinv, float *__restrict__ Vinv32,
+                                                        double *__restrict__ Vsave, int f64_apply,
                                                         int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double(*L)[MAXR + 1] = reinterpret_cast<double(*)[MAXR + 1]>(smem_raw);
@@ -126,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
             for (int k = 0; k < N; k++)
                 if (k != n) v *= G_all[(int64_t)k * RR + idx];
             L[idx / R][idx % R] = v;
+            if (attempt == 0) Vsave[idx] = v;
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -142,19 +160,19 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
             for (int r = threadIdx.x; r < R; r += kThreads) L[r][r] += ridge;
         __syncthreads();
         for (int j = 0; j < R; j++) {
-            // every thread reads the pivot (no serial section)
-            const double d = L[j][j];
-            if (!(d > 0.0)) {
-                if (threadIdx.x == 0) fail = 1;
-                break;
-            }
-            const double ljj = sqrt(d);
-            const double inv = 1.0 / ljj;
-            __syncthreads();  // all threads have read L[j][j]
             if (threadIdx.x == 0) {
-                L[j][j] = ljj;
-                rdiag[j] = inv;
+                const double d = L[j][j];
+                if (!(d > 0.0)) {
+                    fail = 1;
+                } else {
+                    const double ljj = sqrt(d);
+                    L[j][j] = ljj;
+                    rdiag[j] = 1.0 / ljj;
+                }
             }
+            __syncthreads();
+            if (fail) break;
+            const double inv = rdiag[j];
             for (int i = j + 1 + threadIdx.x; i < R; i += kThreads) L[i][j] *= inv;
             __syncthreads();
             const int m = R - j - 1;
@@ -177,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
         }
         return;
     }
-    // L^{-1} column by column (forward substitution on unit vectors)
+    // L^{-1} column by column (forward substitution on unit vectors, FP64)
     for (int c = threadIdx.x; c < R; c += kThreads) {
         for (int i = 0; i < c; i++) Li[i][c] = 0.0;
         Li[c][c] = rdiag[c];
@@ -188,66 +206,81 @@ __global__ void __launch_bounds__(kThreads) k_normal_eq(const double *__restrict
         }
     }
     __syncthreads();
-    // V^{-1} = L^{-T} L^{-1}
-    for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
-        const int i = idx / R, j = idx % R;
-        double s = 0.0;
-        for (int k = max(i, j); k < R; k++) s = fma(Li[k][i], Li[k][j], s);
-        Vinv[idx] = s;
-        Vinv32[idx] = (float)s;
+    // V^{-1} = L^{-T} L^{-1}: FP64 for FP64 factors; otherwise L^{-1} is
+    // rounded to FP32 once (reusing L's storage) and the product runs in FP32
+    if (f64_apply) {
+        for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
+            const int i = idx / R, j = idx % R;
+            double s = 0.0;
+            for (int k = max(i, j); k < R; k++) s = fma(Li[k][i], Li[k][j], s);
+            Vinv[idx] = s;
+            Vinv32[idx] = (float)s;
+        }
+    } else {
+        float(*Lf)[MAXR + 1] = reinterpret_cast<float(*)[MAXR + 1]>(smem_raw);
+        __syncthreads();  // L is no longer read
+        for (int idx = threadIdx.x; idx < RR; idx += kThreads) Lf[idx / R][idx % R] = (float)Li[idx / R][idx % R];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < RR; idx += kThreads) {
+            const int i = idx / R, j = idx % R;
+            float s = 0.0f;
+            for (int k = max(i, j); k < R; k++) s = fmaf(Lf[k][i], Lf[k][j], s);
+            Vinv32[idx] = s;
+        }
     }
 }
 
-// In place M <- M V^{-1} (one warp per row, lane c owns columns c, c+32),
-// plus per-block partials of <M_old(:, c), M_new(:, c)>.
-template <typename C>
+// In place M <- M V^{-1}: one thread per row, V^{-1} broadcast from shared
+// memory (zero-padded to RP columns), CC independent accumulators per
+// thread; the row's inputs are re-read from L1 for each output chunk.
+template <typename C, int RP>
 __global__ void __launch_bounds__(kThreads) k_solve_rows(C *__restrict__ M, int64_t I, int R,
-                                                         const C *__restrict__ Vinv, double *__restrict__ partial) {
-    __shared__ C Vs[MAXR][MAXR];
-    __shared__ double red[kThreads / 32][MAXR];
-    for (int idx = threadIdx.x; idx < R * R; idx += kThreads) Vs[idx / R][idx % R] = Vinv[idx];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c0 = lane, c1 = lane + 32;
-    C d0 = C(0), d1 = C(0);  // this warp's share of <M_old(:,c), M_new(:,c)>
-    for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + warp; i < I; i += (int64_t)gridDim.x * (kThreads / 32)) {
-        C *row = M + i * R;
-        const C x0 = c0 < R ? row[c0] : C(0);
-        const C x1 = c1 < R ? row[c1] : C(0);
-        C y0 = C(0), y1 = C(0);
-        for (int r = 0; r < R; r++) {
-            const C xr = __shfl_sync(0xffffffffu, r < 32 ? x0 : x1, r & 31);
-            if (c0 < R) y0 = fma(xr, Vs[r][c0], y0);
-            if (c1 < R) y1 = fma(xr, Vs[r][c1], y1);
-        }
-        if (c0 < R) {
-            row[c0] = y0;
-            d0 = fma(x0, y0, d0);
-        }
-        if (c1 < R) {
-            row[c1] = y1;
-            d1 = fma(x1, y1, d1);
-        }
+                                                         const C *__restrict__ Vinv) {
+    constexpr int CC = sizeof(C) == 8 ? 16 : 32;  // output columns per pass
+    constexpr int NC = (RP + CC - 1) / CC;
+    __shared__ __align__(16) C Vs[MAXR][NC * CC];
+    for (int idx = threadIdx.x; idx < MAXR * NC * CC; idx += kThreads) {
+        const int r = idx / (NC * CC), c = idx % (NC * CC);
+        Vs[r][c] = (r < R && c < R) ? Vinv[r * R + c] : C(0);
     }
-    red[warp][c0] = (double)d0;
-    red[warp][c1] = (double)d1;
     __syncthreads();
-    for (int c = threadIdx.x; c < R; c += kThreads) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; w++) s += red[w][c];
-        partial[(int64_t)blockIdx.x * MAXR + c] = s;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < I; i += (int64_t)gridDim.x * kThreads) {
+        C *row = M + i * R;
+        C y[NC][CC];
+#pragma unroll
+        for (int q = 0; q < NC; q++)
+#pragma unroll
+            for (int c = 0; c < CC; c++) y[q][c] = C(0);
+#pragma unroll 1
+        for (int r = 0; r < R; r++) {
+            const C xr = row[r];
+#pragma unroll
+            for (int q = 0; q < NC; q++)
+#pragma unroll
+                for (int c = 0; c < CC; c++) y[q][c] = fma(xr, Vs[r][q * CC + c], y[q][c]);
+        }
+#pragma unroll
+        for (int q = 0; q < NC; q++)
+#pragma unroll
+            for (int c = 0; c < CC; c++)
+                if (q * CC + c < R) row[q * CC + c] = y[q][c];
     }
 }
 
-// lambda_r = sqrt(Ghat_rr); G_n = Ghat / (lambda lambda^T); inner_r.
-__global__ void __launch_bounds__(kThreads) k_finish_mode(const double *__restrict__ partial, int nblocks, int R,
+// lambda_r = sqrt(Ghat_rr); G_n = Ghat / (lambda lambda^T); inner_r =
+// <M(:,r), A_n(:,r)> for the normalised A_n. Since M = Ahat V (Ahat = M V^{-1}),
+// <M(:,r), Ahat(:,r)> = sum_s Ghat[r][s] V[s][r], so no pass over the rows
+// is needed.
+__global__ void __launch_bounds__(kThreads) k_finish_mode(const double *__restrict__ V, int R,
                                                           double *__restrict__ lambda, double *__restrict__ G,
                                                           double *__restrict__ inner) {
     __shared__ double lam[MAXR];
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int r = warp; r < R; r += kThreads / 32) {
-        const double s = warp_sum_strided(partial + r, nblocks, MAXR);
-        if ((threadIdx.x & 31) == 0) {
+        double s = 0.0;
+        for (int q = lane; q < R; q += 32) s = fma(G[r * R + q], V[q * R + r], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
             const double l = sqrt(G[r * R + r]);
             lam[r] = l;
             lambda[r] = l;
@@ -335,31 +368,42 @@ cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scra
     return cudaGetLastError();
 }
 
-cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv, float *Vinv32, int *status,
-                             cudaStream_t st) {
+cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv, float *Vinv32, double *Vsave,
+                             int f64_apply, int *status, cudaStream_t st) {
     const size_t smem = 2 * sizeof(double) * MAXR * (MAXR + 1);
     cudaError_t e = cudaFuncSetAttribute(k_normal_eq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_normal_eq<<<1, kThreads, smem, st>>>(G_all, N, n, R, Vinv, Vinv32, status);
+    k_normal_eq<<<1, kThreads, smem, st>>>(G_all, N, n, R, Vinv, Vinv32, Vsave, f64_apply, status);
     return cudaGetLastError();
+}
+
+template <typename C>
+static void solve_rows_rp(C *M, int64_t I, int R, const C *Vinv, int g, cudaStream_t st) {
+    if (R <= 16)
+        k_solve_rows<C, 16><<<g, kThreads, 0, st>>>(M, I, R, Vinv);
+    else if (R <= 32)
+        k_solve_rows<C, 32><<<g, kThreads, 0, st>>>(M, I, R, Vinv);
+    else if (R <= 48)
+        k_solve_rows<C, 48><<<g, kThreads, 0, st>>>(M, I, R, Vinv);
+    else
+        k_solve_rows<C, 64><<<g, kThreads, 0, st>>>(M, I, R, Vinv);
 }
 
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv, const float *Vinv32,
-                              double *scratch, cudaStream_t st) {
-    const int g = rows_grid(I, kThreads / 32);
-    double *partial = scratch + (size_t)GR_BLOCKS * MAXPAIRS;
+                              cudaStream_t st) {
+    if (I == 0) return cudaSuccess;
+    int64_t g64 = (I + kThreads - 1) / kThreads;
+    const int g = (int)(g64 > 152 * 8 ? 152 * 8 : g64);
     if (acc_dtype == RELATE_F64)
-        k_solve_rows<double><<<g, kThreads, 0, st>>>((double *)M, I, R, Vinv, partial);
+        solve_rows_rp<double>((double *)M, I, R, Vinv, g, st);
     else
-        k_solve_rows<float><<<g, kThreads, 0, st>>>((float *)M, I, R, Vinv32, partial);
+        solve_rows_rp<float>((float *)M, I, R, Vinv32, g, st);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish_mode(const double *scratch, int64_t I, int R, double *lambda, double *G_n, double *inner,
+cudaError_t launch_finish_mode(const double *Vsave, int R, double *lambda, double *G_n, double *inner,
                                cudaStream_t st) {
-    const int g = rows_grid(I, kThreads / 32);
-    const double *partial = scratch + (size_t)GR_BLOCKS * MAXPAIRS;
-    k_finish_mode<<<1, kThreads, 0, st>>>(partial, g, R, lambda, G_n, inner);
+    k_finish_mode<<<1, kThreads, 0, st>>>(Vsave, R, lambda, G_n, inner);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,23 @@ __device__ __forceinline__ u128 low_mask(int len) {
     return len >= 128 ? ~(u128)0 : (((u128)1 << len) - 1);
 }
 
+// Integer type wide enough for a position of KW 32-bit limbs: 64-bit
+// arithmetic whenever l(p) <= 64, 128-bit only for the wider keys.
+template <int KW> struct Pos { using T = unsigned long long; };
+template <> struct Pos<4> { using T = u128; };
+
+template <typename P> __device__ __forceinline__ P low_bits(int len) {
+    return len >= (int)(8 * sizeof(P)) ? ~(P)0 : (((P)1 << len) - 1);
+}
+template <int KW> __device__ __forceinline__ typename WordT<KW>::T to_word_p(typename Pos<KW>::T p);
+template <> __device__ __forceinline__ uint32_t to_word_p<1>(unsigned long long p) { return (uint32_t)p; }
+template <> __device__ __forceinline__ unsigned long long to_word_p<2>(unsigned long long p) { return p; }
+template <> __device__ __forceinline__ W128 to_word_p<4>(u128 p) { return to_word<4>(p); }
+template <int KW> __device__ __forceinline__ typename Pos<KW>::T from_word_p(typename WordT<KW>::T w);
+template <> __device__ __forceinline__ unsigned long long from_word_p<1>(uint32_t w) { return w; }
+template <> __device__ __forceinline__ unsigned long long from_word_p<2>(unsigned long long w) { return w; }
+template <> __device__ __forceinline__ u128 from_word_p<4>(W128 w) { return from_word(w); }
+
 // ------------------------------------------------------------------ K1
 template <int KW>
 __global__ void __launch_bounds__(kThreads) k_build_keys(const uint32_t *__restrict__ coords,
@@ -55,20 +72,21 @@ __global__ void __launch_bounds__(kThreads) k_build_keys(const uint32_t *__restr
                                                          typename WordT<KW>::T *__restrict__ keys,
                                                          uint32_t *__restrict__ idx,
                                                          uint32_t *__restrict__ err) {
+    using P = typename Pos<KW>::T;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        u128 p = 0;
+        P p = 0;
         bool bad = false;
         for (int m = 0; m < N; m++) {
             uint32_t c = __ldg(coords + (int64_t)m * n + e);
             bad |= (uint64_t)c >= dims[m];
             for (int r = runs.mode_begin[m]; r < runs.mode_begin[m + 1]; r++) {
-                u128 bits = (u128)((c >> runs.src[r]) & (uint32_t)(((uint64_t)1 << runs.len[r]) - 1));
+                P bits = (P)((c >> runs.src[r]) & (uint32_t)(((uint64_t)1 << runs.len[r]) - 1));
                 p |= bits << runs.dst[r];
             }
         }
         if (bad) atomicOr(err, 1u);
-        keys[e] = to_word<KW>(p);
+        keys[e] = to_word_p<KW>(p);
         idx[e] = (uint32_t)e;
     }
 }
@@ -78,17 +96,18 @@ template <int KW>
 __global__ void __launch_bounds__(kThreads) k_make_words(const typename WordT<KW>::T *__restrict__ keys,
                                                          int64_t n, BitRuns runs,
                                                          typename WordT<KW>::T *__restrict__ words) {
+    using P = typename Pos<KW>::T;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        u128 p = from_word(keys[e]);
-        u128 w = 0;
+        const P p = from_word_p<KW>(keys[e]);
+        P w = 0;
         for (int m = 0; m < kMaxModes; m++) {
             for (int r = runs.mode_begin[m]; r < runs.mode_begin[m + 1]; r++) {
-                u128 bits = (p >> runs.dst[r]) & low_mask(runs.len[r]);
+                const P bits = (p >> runs.dst[r]) & low_bits<P>(runs.len[r]);
                 w |= bits << (runs.field_off[m] + runs.src[r]);
             }
         }
-        words[e] = to_word<KW>(w);
+        words[e] = to_word_p<KW>(w);
     }
 }
 
@@ -96,18 +115,20 @@ template <int KW>
 __global__ void __launch_bounds__(kThreads) k_words_to_keys(const typename WordT<KW>::T *__restrict__ words,
                                                             int64_t n, BitRuns runs,
                                                             unsigned long long *__restrict__ out2) {
+    using P = typename Pos<KW>::T;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        u128 w = from_word(words[e]);
-        u128 p = 0;
+        const P w = from_word_p<KW>(words[e]);
+        P p = 0;
         for (int m = 0; m < kMaxModes; m++) {
             for (int r = runs.mode_begin[m]; r < runs.mode_begin[m + 1]; r++) {
-                u128 bits = (w >> (runs.field_off[m] + runs.src[r])) & low_mask(runs.len[r]);
+                const P bits = (w >> (runs.field_off[m] + runs.src[r])) & low_bits<P>(runs.len[r]);
                 p |= bits << runs.dst[r];
             }
         }
-        out2[2 * e] = (unsigned long long)p;
-        out2[2 * e + 1] = (unsigned long long)(p >> 64);
+        const u128 q = (u128)p;
+        out2[2 * e] = (unsigned long long)q;
+        out2[2 * e + 1] = (unsigned long long)(q >> 64);
     }
 }
 

@@ -153,20 +153,20 @@ size_t dense_scratch_doubles(int R);
 cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G,
                         cudaStream_t st);
 
-// V = Hadamard_{k != n} G_k; Cholesky; Vinv (FP64 and FP32 copies).
+// V = Hadamard_{k != n} G_k (kept in Vsave); FP64 Cholesky; V^{-1} in FP64
+// (f64_apply) or FP32 (Vinv32, always written).
 // status[0] |= 1 on ridge retry, status[1] = 1 if not PD after the retry.
-cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv,
-                             float *Vinv32, int *status, cudaStream_t st);
+cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv, float *Vinv32,
+                             double *Vsave, int f64_apply, int *status, cudaStream_t st);
 
-// Row pass 1: in place, M (I x R, acc dtype) <- M Vinv; per-block partials of
-// the Gram of the result and of <M_old(:,r), result(:,r)>.
+// In place, M (I x R, acc dtype) <- M V^{-1}.
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv,
-                              const float *Vinv32, double *scratch, cudaStream_t st);
+                              const float *Vinv32, cudaStream_t st);
 
-// Reduces the solve partials into lambda, G_n (normalised Gram) and the fit
-// inner products.
-cudaError_t launch_finish_mode(const double *scratch, int64_t I, int R, double *lambda,
-                               double *G_n, double *inner, cudaStream_t st);
+// lambda and the normalised Gram G_n from the raw Gram of M V^{-1} (in G_n),
+// and the fit inner products from that Gram and V.
+cudaError_t launch_finish_mode(const double *Vsave, int R, double *lambda, double *G_n, double *inner,
+                               cudaStream_t st);
 
 // Row pass 2: A_n = Mhat / lambda, stored in the factor dtype.
 cudaError_t launch_scale_store(const void *Mhat, int64_t I, int R, int acc_dtype,

@@ -352,15 +352,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
         auto bin_of = [&](uint32_t row) -> uint32_t {
             return direct ? row - lo : (row * 2654435761u) >> (32 - kSortBinBits);
         };
+        // pass 1 counts rows; the warp-aggregated atomic returns the bin's
+        // running count, so each nonzero learns its offset inside its bin
+        uint32_t ibin[kItems], ioff[kItems];
         if (sorted) {
             for (uint32_t i = threadIdx.x; i < nb; i += kThreads) bins[i] = 0;
             __syncthreads();
-#pragma unroll 4
+#pragma unroll
             for (int i = 0; i < kItems; i++) {
                 const int j = i * kThreads + threadIdx.x;
                 const uint32_t r = j < nt ? bin_of(fld(sw[j], mshift, mmask)) : 0xffffffffu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, r);
-                if (r != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(bins + r, (uint32_t)__popc(peers));
+                const int leader = __ffs(peers) - 1;
+                uint32_t base = 0;
+                if (r != 0xffffffffu && lane == leader) base = atomicAdd(bins + r, (uint32_t)__popc(peers));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                ibin[i] = r;
+                ioff[i] = base + __popc(peers & lane_lt_mask());
             }
             __syncthreads();
             {   // exclusive scan of the nb counters, a contiguous slice per thread
@@ -391,38 +399,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
             }
             __syncthreads();
         }
-        // ---- decode each nonzero once into its record at its (sorted) position
-#pragma unroll 4
+        // ---- pass 2: decode each nonzero once into its record at its (sorted) position
+#pragma unroll
         for (int i = 0; i < kItems; i++) {
             const int j = i * kThreads + threadIdx.x;
-            Word w{};
-            uint32_t row = 0xffffffffu;
-            if (j < nt) {
-                w = sw[j];
-                row = fld(w, mshift, mmask);
-            }
-            uint32_t p = (uint32_t)j;
-            if (sorted) {
-                const uint32_t r = row == 0xffffffffu ? 0xffffffffu : bin_of(row);
-                const uint32_t peers = __match_any_sync(0xffffffffu, r);
-                const int leader = __ffs(peers) - 1;
-                uint32_t p0 = 0;
-                if (r != 0xffffffffu && lane == leader) p0 = atomicAdd(bins + r, (uint32_t)__popc(peers));
-                p0 = __shfl_sync(0xffffffffu, p0, leader);
-                p = p0 + __popc(peers & lane_lt_mask());
-            }
-            if (j < nt) {
-                R_t rec;
-                rec.val = a.vals_f64 ? (C)reinterpret_cast<const double *>(sv)[j]
-                                     : (C)reinterpret_cast<const float *>(sv)[j];
+            if (j >= nt) continue;
+            const Word w = sw[j];
+            const uint32_t p = sorted ? bins[ibin[i]] + ioff[i] : (uint32_t)j;
+            R_t rec;
+            rec.val = a.vals_f64 ? (C)reinterpret_cast<const double *>(sv)[j]
+                                 : (C)reinterpret_cast<const float *>(sv)[j];
 #pragma unroll
-                for (int k = 0; k < NI; k++) rec.idx[k] = k < N ? fld(w, a.rshift[k], a.rmask[k]) : 0u;
-                if (hot_n) {  // slot 0 becomes the run's destination: 0x80000000|slot for a hot row
-                    const uint32_t hs = hot_slot_of(row);
-                    if (hs != 0xffffffffu) rec.idx[0] = 0x80000000u | hs;
-                }
-                *reinterpret_cast<R_t *>(srec + (size_t)p * RB) = rec;
+            for (int k = 0; k < NI; k++) rec.idx[k] = k < N ? fld(w, a.rshift[k], a.rmask[k]) : 0u;
+            if (hot_n) {  // slot 0 becomes the run's destination: 0x80000000|slot for a hot row
+                const uint32_t hs = hot_slot_of(rec.idx[0]);
+                if (hs != 0xffffffffu) rec.idx[0] = 0x80000000u | hs;
             }
+            *reinterpret_cast<R_t *>(srec + (size_t)p * RB) = rec;
         }
         __syncthreads();  // records complete; the raw stage is free
         if (use_tma && threadIdx.x == 0 && tq + gridDim.x < ntiles) {
