@@ -79,10 +79,20 @@ struct relate_handle_s {
            *d_fit = nullptr, *d_V = nullptr;
     float *d_Vinv32 = nullptr;
     int *d_status = nullptr;
+    // the normal equations of mode n run on `aux`, overlapped with mode n's
+    // MTTKRP (they depend only on the other modes' Grams)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_g = nullptr, ev_v = nullptr;
 
     ~relate_handle_s() {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
+        if (aux) {
+            cudaStreamSynchronize(aux);
+            cudaStreamDestroy(aux);
+        }
+        if (ev_g) cudaEventDestroy(ev_g);
+        if (ev_v) cudaEventDestroy(ev_v);
         void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_err, d_M, d_scratch, d_G, d_Vinv,
                         d_lambda, d_inner, d_fit, d_Vinv32, d_status, d_V};
         for (void *p : ptrs)
@@ -197,6 +207,10 @@ int ensure_ws(relate_handle_s *h, int R) {
         (e = cudaMalloc((void **)&h->d_fit, 64)) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_status, 64)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals workspace");
+    if (!h->aux && ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+                    (e = cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
+                    (e = cudaEventCreateWithFlags(&h->ev_v, cudaEventDisableTiming)) != cudaSuccess))
+        return cuda_fail(e, "relate_cpals: auxiliary stream");
     h->ws_R = RM;
     return RELATE_OK;
 }
@@ -423,9 +437,21 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
                 rc = cuda_fail(e, "relate_encode: setup");
                 goto done;
             }
+        // byte tables of the two bit permutations (coordinates -> p, p -> word)
+        std::vector<unsigned char> host_luts(2 * kLutMaxBytes, 0);
+        ByteLuts key_luts{}, word_luts{};
+        build_key_luts(N, h->lbits, h->order, h->lp, h->KW, key_luts, host_luts.data());
+        build_word_luts(N, h->runs.field_off, h->order, h->lp, h->KW, word_luts, host_luts.data() + kLutMaxBytes);
+        void *d_luts = nullptr;
+        if ((e = tmp.alloc(&d_luts, 2 * kLutMaxBytes)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d_luts, host_luts.data(), 2 * kLutMaxBytes, cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess) {
+            rc = cuda_fail(e, "relate_encode: permutation tables");
+            goto done;
+        }
         bool in_alt = false;
-        if ((e = launch_build_keys(h->KW, c_dev, (const uint64_t *)d_dims, nnz, N, h->runs, keys, (uint32_t *)idx,
-                                   d_err, st)) != cudaSuccess ||
+        if ((e = launch_build_keys_lut(h->KW, c_dev, (const uint64_t *)d_dims, nnz, N, key_luts, d_luts, keys,
+                                       (uint32_t *)idx, d_err, st)) != cudaSuccess ||
             (e = radix_sort_pairs(h->KW, keys, (uint32_t *)idx, keys_alt, (uint32_t *)idx_alt, nnz, h->lp, sort_tmp,
                                   sort_bytes, st, &in_alt)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: key build / sort");
@@ -435,7 +461,8 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
         uint32_t *sperm = (uint32_t *)(in_alt ? idx_alt : idx);
         if ((e = cudaMalloc((void **)&h->d_perm, nnz * 4 + 16)) != cudaSuccess ||
             (e = cudaMemcpyAsync(h->d_perm, sperm, nnz * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
-            (e = launch_make_words(h->KW, skeys, nnz, h->runs, h->d_words, st)) != cudaSuccess ||
+            (e = launch_make_words_lut(h->KW, skeys, nnz, word_luts, (const unsigned char *)d_luts + kLutMaxBytes,
+                                       h->d_words, st)) != cudaSuccess ||
             (e = launch_gather(v_dev, sperm, nnz, vb, h->d_vals, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: words / gather");
             goto done;
@@ -540,10 +567,16 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     for (int it = 1; it <= iters; it++) {
         for (int n = 0; n < N; n++) {
             const int64_t In = (int64_t)h->dims[n];
+            // V of mode n (other modes' Grams, all final in stream order) on aux
+            if ((e = cudaEventRecord(h->ev_g, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess ||
+                (e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
+                                      h->d_status, h->aux)) != cudaSuccess ||
+                (e = cudaEventRecord(h->ev_v, h->aux)) != cudaSuccess)
+                return cuda_fail(e, "relate_cpals: normal equations");
             rc = run_mttkrp(h, n, factors, R, h->d_M, st);
             if (rc) return rc;
-            if ((e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
-                                      h->d_status, st)) != cudaSuccess ||
+            if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess ||
                 (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess ||
                 (e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) != cudaSuccess ||
                 (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess ||

@@ -11,6 +11,8 @@
 //      stats        equal-work partitions, per-partition [lo, hi] per mode,
 //                   per-mode run counts and histograms (Sec. 4.1.3, 4.2)
 // All integer work; results are bit-exact with the CPU oracle.
+#include <cstring>
+
 #include "internal.cuh"
 
 namespace relate {
@@ -518,6 +520,49 @@ __global__ void __launch_bounds__(kThreads) k_hot_rows(const uint32_t *__restric
     hot_rows[j] = ((uint64_t)j < I && sorted_keys[j] != 0xffffffffu) ? sorted_idx[j] : 0xffffffffu;
 }
 
+// ---- table-driven bit permutations (K1 key build, p -> word packing)
+template <int KW>
+__global__ void __launch_bounds__(kThreads) k_build_keys_lut(const uint32_t *__restrict__ coords,
+                                                             const uint64_t *__restrict__ dims, int64_t n, int N,
+                                                             ByteLuts d, const typename Pos<KW>::T *__restrict__ tab,
+                                                             typename WordT<KW>::T *__restrict__ keys,
+                                                             uint32_t *__restrict__ idx, uint32_t *__restrict__ err) {
+    using P = typename Pos<KW>::T;
+    extern __shared__ __align__(16) unsigned char lut_raw[];
+    P *lut = reinterpret_cast<P *>(lut_raw);
+    for (int i = threadIdx.x; i < d.ntab * 256; i += blockDim.x) lut[i] = tab[i];
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        P p = 0;
+        bool bad = false;
+        for (int m = 0; m < N; m++) {
+            const uint32_t c = __ldg(coords + (int64_t)m * n + e);
+            bad |= (uint64_t)c >= dims[m];
+            for (int t = d.src_begin[m]; t < d.src_begin[m + 1]; t++) p |= lut[t * 256 + ((c >> (8 * d.byte[t])) & 255u)];
+        }
+        if (bad) atomicOr(err, 1u);
+        keys[e] = to_word_p<KW>(p);
+        idx[e] = (uint32_t)e;
+    }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kThreads) k_make_words_lut(const typename WordT<KW>::T *__restrict__ keys, int64_t n,
+                                                             ByteLuts d, const typename Pos<KW>::T *__restrict__ tab,
+                                                             typename WordT<KW>::T *__restrict__ words) {
+    using P = typename Pos<KW>::T;
+    extern __shared__ __align__(16) unsigned char lut_raw[];
+    P *lut = reinterpret_cast<P *>(lut_raw);
+    for (int i = threadIdx.x; i < d.ntab * 256; i += blockDim.x) lut[i] = tab[i];
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const P p = from_word_p<KW>(keys[e]);
+        P w = 0;
+        for (int t = 0; t < d.ntab; t++) w |= lut[t * 256 + (uint32_t)((p >> (8 * d.byte[t])) & 255u)];
+        words[e] = to_word_p<KW>(w);
+    }
+}
+
 inline int grid_for(int64_t n, int per_block = kThreads, int cap = 152 * 32) {
     int64_t g = (n + per_block - 1) / per_block;
     if (g < 1) g = 1;
@@ -655,6 +700,101 @@ cudaError_t launch_partition_stats(int KW, const void *words, int64_t n, int N, 
 cudaError_t launch_hist_summary(const uint32_t *counts, uint64_t len, unsigned long long *out2, cudaStream_t st) {
     if (len == 0) return cudaSuccess;
     k_hist_summary<<<grid_for((int64_t)len), kThreads, 0, st>>>(counts, len, out2);
+    return cudaGetLastError();
+}
+
+namespace {
+// table entries have the width of the arithmetic type: 8 bytes for keys of
+// up to 64 bits, 16 bytes beyond
+inline size_t entry_bytes(int KW) { return KW == 4 ? 16 : 8; }
+// sets bit `bit` of table entry `e` (little-endian 32-bit limbs)
+inline void set_bit(unsigned char *tables, int KW, size_t e, int bit) {
+    uint32_t *limbs = reinterpret_cast<uint32_t *>(tables + e * entry_bytes(KW));
+    limbs[bit >> 5] |= 1u << (bit & 31);
+}
+}  // namespace
+
+void build_key_luts(int N, const int *lbits, const int8_t *order, int lp, int KW, ByteLuts &d, void *host_tables) {
+    // bit s of coordinate m lands at position pos[m][s] of p
+    int pos[kMaxModes][32];
+    int next[kMaxModes] = {};
+    for (int t = 0; t < lp; t++) pos[order[t]][next[order[t]]++] = t;
+    unsigned char *tab = static_cast<unsigned char *>(host_tables);
+    d.ntab = 0;
+    for (int m = 0; m < kMaxModes; m++) {
+        d.src_begin[m] = d.ntab;
+        if (m >= N) continue;
+        for (int b = 0; b * 8 < lbits[m]; b++) {
+            const int t = d.ntab++;
+            d.byte[t] = (uint8_t)b;
+            memset(tab + (size_t)t * 256 * entry_bytes(KW), 0, 256 * entry_bytes(KW));
+            for (int v = 0; v < 256; v++)
+                for (int i = 0; i < 8; i++) {
+                    const int s = 8 * b + i;
+                    if (s < lbits[m] && ((v >> i) & 1)) set_bit(tab, KW, (size_t)t * 256 + v, pos[m][s]);
+                }
+        }
+    }
+    d.src_begin[kMaxModes] = d.ntab;
+}
+
+void build_word_luts(int N, const int *field_off, const int8_t *order, int lp, int KW, ByteLuts &d,
+                     void *host_tables) {
+    // bit t of p is bit c_t of mode a_t, which sits at field_off[a_t] + c_t
+    int dst[RELATE_MAX_KEY_BITS];
+    int next[kMaxModes] = {};
+    for (int t = 0; t < lp; t++) {
+        const int m = order[t];
+        dst[t] = field_off[m] + next[m]++;
+    }
+    (void)N;
+    unsigned char *tab = static_cast<unsigned char *>(host_tables);
+    d.ntab = 0;
+    for (int b = 0; b * 8 < lp; b++) {
+        const int t = d.ntab++;
+        d.byte[t] = (uint8_t)b;
+        memset(tab + (size_t)t * 256 * entry_bytes(KW), 0, 256 * entry_bytes(KW));
+        for (int v = 0; v < 256; v++)
+            for (int i = 0; i < 8; i++) {
+                const int bit = 8 * b + i;
+                if (bit < lp && ((v >> i) & 1)) set_bit(tab, KW, (size_t)t * 256 + v, dst[bit]);
+            }
+    }
+    for (int m = 0; m <= kMaxModes; m++) d.src_begin[m] = 0;
+}
+
+cudaError_t launch_build_keys_lut(int KW, const uint32_t *coords, const uint64_t *dims_dev, int64_t n, int N,
+                                  const ByteLuts &d, const void *tables, void *keys, uint32_t *idx, uint32_t *err,
+                                  cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int g = grid_for(n, kThreads, 152 * 8);
+    const size_t smem = (size_t)d.ntab * 256 * entry_bytes(KW);
+    switch (KW) {
+    case 1: k_build_keys_lut<1><<<g, kThreads, smem, st>>>(coords, dims_dev, n, N, d, (const unsigned long long *)tables, (uint32_t *)keys, idx, err); break;
+    case 2: k_build_keys_lut<2><<<g, kThreads, smem, st>>>(coords, dims_dev, n, N, d, (const unsigned long long *)tables, (unsigned long long *)keys, idx, err); break;
+    default: {
+        cudaError_t e = cudaFuncSetAttribute(k_build_keys_lut<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_build_keys_lut<4><<<g, kThreads, smem, st>>>(coords, dims_dev, n, N, d, (const u128 *)tables, (W128 *)keys, idx, err);
+    }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_words_lut(int KW, const void *keys, int64_t n, const ByteLuts &d, const void *tables,
+                                  void *words, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int g = grid_for(n, kThreads, 152 * 8);
+    const size_t smem = (size_t)d.ntab * 256 * entry_bytes(KW);
+    switch (KW) {
+    case 1: k_make_words_lut<1><<<g, kThreads, smem, st>>>((const uint32_t *)keys, n, d, (const unsigned long long *)tables, (uint32_t *)words); break;
+    case 2: k_make_words_lut<2><<<g, kThreads, smem, st>>>((const unsigned long long *)keys, n, d, (const unsigned long long *)tables, (unsigned long long *)words); break;
+    default: {
+        cudaError_t e = cudaFuncSetAttribute(k_make_words_lut<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_make_words_lut<4><<<g, kThreads, smem, st>>>((const W128 *)keys, n, d, (const u128 *)tables, (W128 *)words);
+    }
+    }
     return cudaGetLastError();
 }
 

@@ -63,6 +63,28 @@ cudaError_t radix_sort_pairs(int KW, void *keys, uint32_t *vals, void *keys_alt,
                              int64_t n, int lp, void *temp, size_t temp_bytes, cudaStream_t st,
                              bool *in_alt);
 
+// Table-driven bit permutation: table t (256 entries of the position /
+// word type) maps the 8 bits of input byte `byte[t]` of input `src[t]` to
+// their output bits. For the key build the inputs are the N coordinates,
+// for the word packing the single input p.
+struct ByteLuts {
+    int ntab;
+    int src_begin[kMaxModes + 1];  // tables of input m: [src_begin[m], src_begin[m+1])
+    uint8_t byte[32];
+};
+// Builds the tables on the host (entries of 8 bytes for KW <= 2, 16 for KW = 4).
+void build_key_luts(int N, const int *lbits, const int8_t *order, int lp, int KW, ByteLuts &d,
+                    void *host_tables);
+void build_word_luts(int N, const int *field_off, const int8_t *order, int lp, int KW, ByteLuts &d,
+                     void *host_tables);
+constexpr size_t kLutMaxBytes = 32 * 256 * 16;
+
+cudaError_t launch_build_keys_lut(int KW, const uint32_t *coords, const uint64_t *dims_dev, int64_t n, int N,
+                                  const ByteLuts &d, const void *tables, void *keys, uint32_t *idx, uint32_t *err,
+                                  cudaStream_t st);
+cudaError_t launch_make_words_lut(int KW, const void *keys, int64_t n, const ByteLuts &d, const void *tables,
+                                  void *words, cudaStream_t st);
+
 // p (sorted) -> stored word with concatenated coordinate fields.
 cudaError_t launch_make_words(int KW, const void *keys, int64_t n, const BitRuns &runs, void *words,
                               cudaStream_t st);

@@ -14,8 +14,9 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
     const int accb = mttkrp_acc_bytes(factor_dtype);
     const int fb = factor_dtype == RELATE_F64 ? 8 : factor_dtype == RELATE_F32 ? 4 : 2;
 
-    // 16-byte vector path: every factor row starts 16-byte aligned
-    bool vec_ok = (a.R * fb) % 16 == 0 && (reinterpret_cast<uintptr_t>(a.out) % 16) == 0;
+    // vector path (16-byte loads, 8-byte for BF16): every factor row starts
+    // 16-byte aligned and the output rows take 16-byte vector atomics
+    bool vec_ok = (a.R * fb) % 16 == 0 && (a.R * accb) % 16 == 0 && (reinterpret_cast<uintptr_t>(a.out) % 16) == 0;
     for (int k = 0; k < a.N; k++)
         if (k != a.mode && (reinterpret_cast<uintptr_t>(a.factors[k]) % 16) != 0) vec_ok = false;
 

@@ -39,7 +39,7 @@ template <> struct Prec<float> {
 };
 template <> struct Prec<__nv_bfloat16> {
     using C = float;
-    static constexpr int VEC = 8;
+    static constexpr int VEC = 4;  // 8-byte loads: 8 lanes per nonzero for R = 32
 };
 
 template <int KW> __device__ __forceinline__ typename WordT<KW>::T load_word(const void *p, int64_t j);
@@ -88,6 +88,15 @@ template <> struct VecLoad<float, 4> {
         x[3] = v.w;
     }
 };
+template <> struct VecLoad<__nv_bfloat16, 4> {
+    static __device__ __forceinline__ void run(const __nv_bfloat16 *row, int j, float (&x)[4]) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row) + j);
+        x[0] = __uint_as_float(u.x << 16);
+        x[1] = __uint_as_float(u.x & 0xffff0000u);
+        x[2] = __uint_as_float(u.y << 16);
+        x[3] = __uint_as_float(u.y & 0xffff0000u);
+    }
+};
 template <> struct VecLoad<__nv_bfloat16, 8> {
     static __device__ __forceinline__ void run(const __nv_bfloat16 *row, int j, float (&x)[8]) {
         uint4 u = __ldg(reinterpret_cast<const uint4 *>(row) + j);
@@ -132,7 +141,6 @@ template <typename C> struct GAdd<C, 1> {
 // Nonzeros a group keeps in flight: all factor-row loads of U nonzeros are
 // issued before any of them is consumed.
 template <typename FT, int VPL> struct Unroll { static constexpr int U = 4; };
-template <int VPL> struct Unroll<__nv_bfloat16, VPL> { static constexpr int U = 2; };
 
 constexpr int kTile = 2048;       // nonzeros per tile
 constexpr int kItems = kTile / kThreads;
