@@ -577,11 +577,25 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
             rc = run_mttkrp(h, n, factors, R, h->d_M, st);
             if (rc) return rc;
             if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess ||
-                (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess ||
-                (e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) != cudaSuccess ||
-                (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess ||
-                (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype, st)) !=
-                    cudaSuccess)
+                (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess)
+                return cuda_fail(e, "relate_cpals: mode update");
+            if (h->factor_dtype == RELATE_BF16 && gram_tc_supported(R)) {
+                // lambda from Ahat's column norms, store the normalised BF16
+                // factor, then its Gram on the tensor cores (of the stored values)
+                if ((e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
+                    (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
+                                            st)) != cudaSuccess ||
+                    (e = launch_gram(factors[n], In, R, RELATE_BF16, h->d_scratch, h->d_G + n * RR, st)) !=
+                        cudaSuccess ||
+                    (e = launch_inner_from_gram(h->d_V, h->d_G + n * RR, h->d_lambda, R, h->d_inner, st)) !=
+                        cudaSuccess)
+                    return cuda_fail(e, "relate_cpals: mode update");
+            } else if ((e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) !=
+                           cudaSuccess ||
+                       (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) !=
+                           cudaSuccess ||
+                       (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
+                                               st)) != cudaSuccess)
                 return cuda_fail(e, "relate_cpals: mode update");
         }
         if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess)

@@ -295,6 +295,53 @@ __global__ void __launch_bounds__(kThreads) k_finish_mode(const double *__restri
     }
 }
 
+// Per-block column sums of squares of Ahat (FP32 rows, FP64 partials): the
+// column norms lambda of the BF16 path, before its factor is rounded.
+__global__ void __launch_bounds__(kThreads) k_colsq_partial(const float *__restrict__ M, int64_t I, int R,
+                                                            double *__restrict__ partial) {
+    __shared__ float red[kThreads / 32][MAXR];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = lane, c1 = lane + 32;
+    float s0 = 0.f, s1 = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + warp; i < I; i += (int64_t)gridDim.x * (kThreads / 32)) {
+        const float *row = M + i * R;
+        if (c0 < R) s0 = fmaf(row[c0], row[c0], s0);
+        if (c1 < R) s1 = fmaf(row[c1], row[c1], s1);
+    }
+    red[warp][c0] = s0;
+    red[warp][c1] = s1;
+    __syncthreads();
+    for (int c = threadIdx.x; c < R; c += kThreads) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; w++) t += (double)red[w][c];
+        partial[(int64_t)blockIdx.x * MAXR + c] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_colnorm_finish(const double *__restrict__ partial, int nblocks, int R,
+                                                             double *__restrict__ lambda) {
+    const int warp = threadIdx.x >> 5;
+    for (int r = warp; r < R; r += kThreads / 32) {
+        const double s = warp_sum_strided(partial + r, nblocks, MAXR);
+        if ((threadIdx.x & 31) == 0) lambda[r] = sqrt(s);
+    }
+}
+
+// inner_r = <M(:,r), A_n(:,r)> from the Gram G_n of the stored (normalised)
+// A_n: M = Ahat V and Ahat = A_n diag(lambda), so inner_r = sum_s lambda_s
+// G_n[r][s] V[s][r].
+__global__ void __launch_bounds__(kThreads) k_inner_from_gram(const double *__restrict__ V, const double *__restrict__ G,
+                                                              const double *__restrict__ lambda, int R,
+                                                              double *__restrict__ inner) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < R; r += kThreads / 32) {
+        double s = 0.0;
+        for (int q = lane; q < R; q += 32) s = fma(lambda[q] * G[r * R + q], V[q * R + r], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) inner[r] = s;
+    }
+}
+
 template <typename C, typename FT> __device__ __forceinline__ FT store_as(C x);
 template <> __device__ __forceinline__ double store_as<double, double>(double x) { return x; }
 template <> __device__ __forceinline__ float store_as<float, float>(float x) { return x; }
@@ -357,6 +404,16 @@ size_t dense_scratch_doubles(int R) {
 cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, cudaStream_t st) {
     if (R < 1 || R > MAXR) return cudaErrorInvalidValue;
     if (I == 0) return cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
+    const int npairs_tc = R * (R + 1) / 2;
+    if (dtype == RELATE_BF16 && gram_tc_supported(R) && (reinterpret_cast<uintptr_t>(A) % 16) == 0) {
+        // BF16 inputs: tcgen05 tensor cores, FP32 accumulation per block
+        int *err = reinterpret_cast<int *>(scratch + (size_t)GR_BLOCKS * MAXPAIRS + (size_t)GR_BLOCKS * MAXR);
+        const int g = gram_tc_blocks(I);
+        cudaError_t e = launch_gram_tc((const __nv_bfloat16 *)A, I, R, scratch, err, st);
+        if (e != cudaSuccess) return e;
+        k_gram_reduce<<<(npairs_tc + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(scratch, g, R, G);
+        return cudaGetLastError();
+    }
     const int g = rows_grid(I, GR_ROWS);
     switch (dtype) {
     case RELATE_F64: k_gram_partial<double><<<g, kThreads, 0, st>>>((const double *)A, I, R, scratch); break;
@@ -398,6 +455,20 @@ cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const do
         solve_rows_rp<double>((double *)M, I, R, Vinv, g, st);
     else
         solve_rows_rp<float>((float *)M, I, R, Vinv32, g, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colnorms(const float *M, int64_t I, int R, double *scratch, double *lambda, cudaStream_t st) {
+    const int g = rows_grid(I, kThreads / 32);
+    double *partial = scratch + (size_t)GR_BLOCKS * MAXPAIRS;
+    k_colsq_partial<<<g, kThreads, 0, st>>>(M, I, R, partial);
+    k_colnorm_finish<<<1, kThreads, 0, st>>>(partial, g, R, lambda);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inner_from_gram(const double *Vsave, const double *G_n, const double *lambda, int R, double *inner,
+                                   cudaStream_t st) {
+    k_inner_from_gram<<<1, kThreads, 0, st>>>(Vsave, G_n, lambda, R, inner);
     return cudaGetLastError();
 }
 

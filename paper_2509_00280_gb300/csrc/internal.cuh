@@ -175,6 +175,13 @@ size_t dense_scratch_doubles(int R);
 cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G,
                         cudaStream_t st);
 
+// Tensor-core Gram partials for BF16 A (R % 8 == 0, R <= 64): one FP64
+// upper-triangle partial per block (gram_tc_blocks(I) blocks); err |= 2 and
+// NaN partials if a bounded wait on the tensor cores gave up.
+bool gram_tc_supported(int R);
+int gram_tc_blocks(int64_t I);
+cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err, cudaStream_t st);
+
 // V = Hadamard_{k != n} G_k (kept in Vsave); FP64 Cholesky; V^{-1} in FP64
 // (f64_apply) or FP32 (Vinv32, always written).
 // status[0] |= 1 on ridge retry, status[1] = 1 if not PD after the retry.
@@ -189,6 +196,12 @@ cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const do
 // and the fit inner products from that Gram and V.
 cudaError_t launch_finish_mode(const double *Vsave, int R, double *lambda, double *G_n, double *inner,
                                cudaStream_t st);
+
+// BF16 path: lambda = column norms of Ahat (FP32), and the fit inner
+// products from the Gram of the stored, normalised BF16 factor.
+cudaError_t launch_colnorms(const float *M, int64_t I, int R, double *scratch, double *lambda, cudaStream_t st);
+cudaError_t launch_inner_from_gram(const double *Vsave, const double *G_n, const double *lambda, int R,
+                                   double *inner, cudaStream_t st);
 
 // Row pass 2: A_n = Mhat / lambda, stored in the factor dtype.
 cudaError_t launch_scale_store(const void *Mhat, int64_t I, int R, int acc_dtype,

@@ -177,3 +177,17 @@ def test_gram():
             # sqrt(660) * 2^-24 = 1.5e-6 relative; FP64 inputs stay in FP64
             tol = 1e-13 if dt == "f64" else 2e-5
             assert rel_fro(G.cpu().numpy(), ref) <= tol, (I, R, dt)
+
+
+@pytest.mark.parametrize("I,R", [(1, 8), (127, 24), (128, 40), (129, 56), (5000, 64), (100_003, 32), (0, 16)])
+def test_gram_bf16_tensor_cores_exact_on_integers(I, R):
+    """BF16 inputs (R a multiple of 8) run on the tcgen05 tensor cores. With
+    small integer entries every product and partial sum is exact in FP32, so
+    the result must equal the exact integer Gram bit for bit."""
+    rng = np.random.default_rng(I + R)
+    A = rng.integers(-3, 4, (I, R)).astype(np.float64)
+    t = factors_dev([A], "bf16")[0] if I else torch.zeros((0, R), dtype=torch.bfloat16, device=DEV)
+    G = torch.full((R, R), float("nan"), dtype=torch.float64, device=DEV)
+    rl.relate_gram(t, R, "bf16", G)
+    torch.cuda.synchronize()
+    assert np.array_equal(G.cpu().numpy(), A.T @ A)
