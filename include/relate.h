@@ -156,7 +156,7 @@ typedef struct {
  * factors: host array of nmodes DEVICE pointers (handle's factor dtype),
  * in = initial factors, out = normalised factors. lambda: HOST, R doubles,
  * out. info: nullable. Runs on the handle's stream; synchronises once per
- * iteration (the fit). Errors: INVALID_ARG, NOT_PD, OOM, CUDA. */
+ * iteration (the fit). Errors: INVALID_ARG, NOT_PD, OOM, TIMEOUT, CUDA. */
 int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *factors,
                  double *lambda, relate_cpals_info_t *info);
 
@@ -192,6 +192,32 @@ int relate_set_precision(relate_handle_t h, relate_dtype_t factor_dtype, relate_
 
 /* Changes the stream used by relate_cpals. */
 int relate_set_stream(relate_handle_t h, void *stream);
+
+typedef struct {
+    uint64_t encode_peak;      /* relate_encode's peak: resident + temporaries */
+    uint64_t resident;         /* held by the handle after relate_encode */
+    uint64_t cpals_workspace;  /* added to the handle by relate_cpals at rank R */
+    uint64_t factors;          /* caller-owned factors: sum_n I_n * R * dtype */
+} relate_footprint_t;
+
+/* Device bytes requested from the stream-ordered allocator by relate_encode
+ * and relate_cpals for a tensor of this shape, before the allocator's own
+ * rounding (a serving layer admits requests by this). A request's peak is
+ * max(encode_peak, resident + cpals_workspace) + factors. Host only: makes no
+ * CUDA call, needs no GPU. The paper has no counterpart. Errors: INVALID_ARG,
+ * KEY_TOO_WIDE. */
+int relate_footprint(const uint64_t *dims, int nmodes, int64_t nnz, const relate_params_t *params, int R,
+                     relate_footprint_t *out);
+
+/* enable != 0: relate_cpals captures one ALS iteration (every mode's MTTKRP,
+ * normal equations, solve, Gram and normalisation, the fit, and the copy of
+ * the fit and status words to pinned host memory) as a CUDA graph once per
+ * call and replays it each iteration, instead of issuing the ~8N launches of
+ * an iteration one by one. Results are those of the plain path (same kernels
+ * in the same order). Needs a non-default stream (relate_set_stream); on the
+ * legacy default stream the plain path runs. Default: disabled. The paper
+ * has no counterpart (launch overhead only). Errors: INVALID_ARG. */
+int relate_set_cpals_graph(relate_handle_t h, int enable);
 
 /* Copies the encoded stream out, in encoded (sorted) order, to DEVICE
  * buffers: coords_out N x nnz uint32 SoA (nullable), vals_out nnz values in

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -34,6 +35,56 @@ bool valid_precision(int f, int a) {
 }
 
 int dtype_bytes(int d) { return d == RELATE_F64 ? 8 : d == RELATE_F32 ? 4 : 2; }
+
+// Device bytes of each allocation. relate_encode, the CP-ALS workspace and
+// relate_footprint all size their buffers from these.
+// 64 bytes of tail padding: tile copies round their size up to 16 bytes
+size_t words_bytes(int64_t nnz, size_t kb) { return (size_t)nnz * kb + 64; }
+size_t vals_bytes(int64_t nnz, int vb) { return (size_t)nnz * vb + 64; }
+size_t bounds_bytes(int64_t P, int N) { return (size_t)(P + 1) * N * 4; }
+size_t perm_bytes(int64_t nnz) { return (size_t)nnz * 4 + 16; }
+constexpr size_t kSmallBytes = 8 * (1 + 3 * kMaxModes) + 1024 * 8;
+
+struct WsSizes {
+    size_t M, scratch, G, RR8, RR4, R8;
+};
+WsSizes ws_sizes(uint64_t maxI, int N, int R) {
+    return WsSizes{maxI * R * 8 + 16, dense_scratch_doubles(R) * 8, (size_t)N * R * R * 8, (size_t)R * R * 8,
+                   (size_t)R * R * 4, (size_t)R * 8};
+}
+size_t ws_total(uint64_t maxI, int N, int R) {
+    const WsSizes w = ws_sizes(maxI, N, R);
+    return w.M + w.scratch + w.G + 2 * w.RR8 + w.RR4 + 2 * w.R8 + 64 + 64;
+}
+
+// Pinned host words for the per-iteration fit / status read-back, handed out
+// in 64-byte slots from page-locked chunks that live until the process exits
+// (freeing page-locked memory synchronises the device, which would stall the
+// other streams of a serving process at every handle release).
+class PinnedSlots {
+  public:
+    double *get() {
+        std::lock_guard<std::mutex> lock(mu_);
+        if (free_.empty()) {
+            void *chunk = nullptr;
+            if (cudaMallocHost(&chunk, kChunk * kSlot) != cudaSuccess) return nullptr;
+            for (int i = kChunk - 1; i >= 0; i--) free_.push_back(static_cast<char *>(chunk) + (size_t)i * kSlot);
+        }
+        char *p = free_.back();
+        free_.pop_back();
+        return reinterpret_cast<double *>(p);
+    }
+    void put(double *p) {
+        std::lock_guard<std::mutex> lock(mu_);
+        free_.push_back(reinterpret_cast<char *>(p));
+    }
+
+  private:
+    static constexpr int kChunk = 256, kSlot = 64;
+    std::mutex mu_;
+    std::vector<char *> free_;
+};
+PinnedSlots g_pinned;
 
 }  // namespace
 
@@ -83,24 +134,31 @@ struct relate_handle_s {
     // MTTKRP (they depend only on the other modes' Grams)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_g = nullptr, ev_v = nullptr;
+    int use_graph = 0;           // relate_cpals replays a captured iteration
+    double *h_pinned = nullptr;  // pinned host words: fit, status[2], err
 
+    // Device memory comes from the stream-ordered allocator and goes back to
+    // it on the handle's stream once that stream and `aux` are idle, so the
+    // release never waits for other streams' work.
     ~relate_handle_s() {
-        if (stream) cudaStreamSynchronize(stream);
-        else cudaDeviceSynchronize();
         if (aux) {
             cudaStreamSynchronize(aux);
             cudaStreamDestroy(aux);
         }
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
         if (ev_g) cudaEventDestroy(ev_g);
         if (ev_v) cudaEventDestroy(ev_v);
+        if (h_pinned) g_pinned.put(h_pinned);
         void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_err, d_M, d_scratch, d_G, d_Vinv,
                         d_lambda, d_inner, d_fit, d_Vinv32, d_status, d_V};
         for (void *p : ptrs)
-            if (p) cudaFree(p);
+            if (p) cudaFreeAsync(p, stream);
         for (auto *p : d_counts)
-            if (p) cudaFree(p);
+            if (p) cudaFreeAsync(p, stream);
         for (auto *p : d_hot_rows)
-            if (p) cudaFree(p);
+            if (p) cudaFreeAsync(p, stream);
+        cudaStreamSynchronize(stream);
     }
 };
 
@@ -182,11 +240,13 @@ struct AsyncBufs {
 
 int ensure_ws(relate_handle_s *h, int R) {
     if (h->ws_R >= R && h->d_M) return RELATE_OK;
+    const cudaStream_t st = h->stream;
     void *ptrs[] = {h->d_M, h->d_scratch, h->d_G, h->d_Vinv, h->d_lambda, h->d_inner, h->d_fit, h->d_Vinv32,
                     h->d_status, h->d_V};
-    cudaStreamSynchronize(h->stream);
+    // earlier iterations on aux are joined into `st` before their results are
+    // used, so stream order on `st` covers every use of the old buffers
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, st);
     h->d_M = nullptr;
     h->d_scratch = h->d_G = h->d_Vinv = h->d_lambda = h->d_inner = h->d_fit = h->d_V = nullptr;
     h->d_Vinv32 = nullptr;
@@ -194,24 +254,24 @@ int ensure_ws(relate_handle_s *h, int R) {
     h->ws_R = 0;
     uint64_t maxI = 0;
     for (int m = 0; m < h->N; m++) maxI = h->dims[m] > maxI ? h->dims[m] : maxI;
-    const int RM = RELATE_MAX_RANK;
+    const WsSizes w = ws_sizes(maxI, h->N, R);
     cudaError_t e;
-    if ((e = cudaMalloc(&h->d_M, maxI * RM * 8 + 16)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_scratch, dense_scratch_doubles(RM) * 8)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_G, (size_t)h->N * RM * RM * 8)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_Vinv, RM * RM * 8)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_V, RM * RM * 8)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_Vinv32, RM * RM * 4)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_lambda, RM * 8)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_inner, RM * 8)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_fit, 64)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_status, 64)) != cudaSuccess)
+    if ((e = cudaMallocAsync(&h->d_M, w.M, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_scratch, w.scratch, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_G, w.G, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_Vinv, w.RR8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_V, w.RR8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_Vinv32, w.RR4, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_lambda, w.R8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_inner, w.R8, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_fit, 64, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&h->d_status, 64, st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals workspace");
     if (!h->aux && ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
                     (e = cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
                     (e = cudaEventCreateWithFlags(&h->ev_v, cudaEventDisableTiming)) != cudaSuccess))
         return cuda_fail(e, "relate_cpals: auxiliary stream");
-    h->ws_R = RM;
+    h->ws_R = R;
     return RELATE_OK;
 }
 
@@ -239,6 +299,54 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
     if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp memset");
     e = launch_mttkrp(a, h->KW, h->factor_dtype, h->val_dtype, h->smem_budget, h->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp launch");
+    return RELATE_OK;
+}
+
+// One ALS sweep over all modes plus the fit, enqueued on the handle's stream
+// (capturable): results land in the pinned host words fit / status.
+int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_fit, int *p_stat) {
+    const cudaStream_t st = h->stream;
+    const int N = h->N;
+    const int RR = R * R;
+    cudaError_t e;
+    for (int n = 0; n < N; n++) {
+        const int64_t In = (int64_t)h->dims[n];
+        // V of mode n (other modes' Grams, all final in stream order) on aux
+        if ((e = cudaEventRecord(h->ev_g, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess ||
+            (e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
+                                  h->d_status, h->aux)) != cudaSuccess ||
+            (e = cudaEventRecord(h->ev_v, h->aux)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: normal equations");
+        int rc = run_mttkrp(h, n, factors, R, h->d_M, st);
+        if (rc) return rc;
+        if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess ||
+            (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: mode update");
+        if (h->factor_dtype == RELATE_BF16 && gram_tc_supported(R)) {
+            // lambda from Ahat's column norms, store the normalised BF16
+            // factor, then its Gram on the tensor cores (of the stored values)
+            if ((e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
+                (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
+                                        st)) != cudaSuccess ||
+                (e = launch_gram(factors[n], In, R, RELATE_BF16, h->d_scratch, h->d_G + n * RR, st)) !=
+                    cudaSuccess ||
+                (e = launch_inner_from_gram(h->d_V, h->d_G + n * RR, h->d_lambda, R, h->d_inner, st)) !=
+                    cudaSuccess)
+                return cuda_fail(e, "relate_cpals: mode update");
+        } else if ((e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) !=
+                       cudaSuccess ||
+                   (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) !=
+                       cudaSuccess ||
+                   (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
+                                           st)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: mode update");
+    }
+    if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p_fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p_stat, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p_stat + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals: fit");
     return RELATE_OK;
 }
 
@@ -382,26 +490,26 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
         const size_t sort_bytes = radix_sort_temp_bytes(nnz);
         // persistent encoding arrays
         // 64 bytes of tail padding: tile copies round their size up to 16 bytes
-        if ((e = cudaMalloc(&h->d_words, nnz * kb + 64)) != cudaSuccess ||
-            (e = cudaMalloc(&h->d_vals, nnz * vb + 64)) != cudaSuccess ||
-            (e = cudaMalloc((void **)&h->d_plo, (h->P + 1) * N * 4)) != cudaSuccess ||
-            (e = cudaMalloc((void **)&h->d_phi, (h->P + 1) * N * 4)) != cudaSuccess ||
-            (e = cudaMalloc((void **)&h->d_normX2, 64)) != cudaSuccess ||
-            (e = cudaMalloc((void **)&h->d_err, 16)) != cudaSuccess ||
+        if ((e = cudaMallocAsync(&h->d_words, words_bytes(nnz, kb), st)) != cudaSuccess ||
+            (e = cudaMallocAsync(&h->d_vals, vals_bytes(nnz, vb), st)) != cudaSuccess ||
+            (e = cudaMallocAsync((void **)&h->d_plo, bounds_bytes(h->P, N), st)) != cudaSuccess ||
+            (e = cudaMallocAsync((void **)&h->d_phi, bounds_bytes(h->P, N), st)) != cudaSuccess ||
+            (e = cudaMallocAsync((void **)&h->d_normX2, 64, st)) != cudaSuccess ||
+            (e = cudaMallocAsync((void **)&h->d_err, 16, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(h->d_err, 0, 16, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: allocation");
             goto done;
         }
         for (int m = 0; m < N; m++)
-            if ((e = cudaMalloc((void **)&h->d_counts[m], h->dims[m] * 4)) != cudaSuccess ||
-                (e = cudaMalloc((void **)&h->d_hot_rows[m], kHotMax * 4)) != cudaSuccess) {
+            if ((e = cudaMallocAsync((void **)&h->d_counts[m], h->dims[m] * 4, st)) != cudaSuccess ||
+                (e = cudaMallocAsync((void **)&h->d_hot_rows[m], kHotMax * 4, st)) != cudaSuccess) {
                 rc = cuda_fail(e, "relate_encode: allocation");
                 goto done;
             }
         if ((e = tmp.alloc(&keys, nnz * kb)) != cudaSuccess || (e = tmp.alloc(&keys_alt, nnz * kb)) != cudaSuccess ||
             (e = tmp.alloc(&idx, nnz * 4)) != cudaSuccess || (e = tmp.alloc(&idx_alt, nnz * 4)) != cudaSuccess ||
             (e = tmp.alloc(&sort_tmp, sort_bytes)) != cudaSuccess || (e = tmp.alloc(&d_dims, 64)) != cudaSuccess ||
-            (e = tmp.alloc(&d_small, 8 * (1 + 3 * kMaxModes) + 1024 * 8)) != cudaSuccess) {
+            (e = tmp.alloc(&d_small, kSmallBytes)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: temporary allocation");
             goto done;
         }
@@ -443,7 +551,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
         build_key_luts(N, h->lbits, h->order, h->lp, h->KW, key_luts, host_luts.data());
         build_word_luts(N, h->runs.field_off, h->order, h->lp, h->KW, word_luts, host_luts.data() + kLutMaxBytes);
         void *d_luts = nullptr;
-        if ((e = tmp.alloc(&d_luts, 2 * kLutMaxBytes)) != cudaSuccess ||
+        if ((e = tmp.alloc(&d_luts, 2 * (size_t)kLutMaxBytes)) != cudaSuccess ||
             (e = cudaMemcpyAsync(d_luts, host_luts.data(), 2 * kLutMaxBytes, cudaMemcpyHostToDevice, st)) !=
                 cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: permutation tables");
@@ -459,7 +567,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
         }
         void *skeys = in_alt ? keys_alt : keys;
         uint32_t *sperm = (uint32_t *)(in_alt ? idx_alt : idx);
-        if ((e = cudaMalloc((void **)&h->d_perm, nnz * 4 + 16)) != cudaSuccess ||
+        if ((e = cudaMallocAsync((void **)&h->d_perm, perm_bytes(nnz), st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(h->d_perm, sperm, nnz * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
             (e = launch_make_words_lut(h->KW, skeys, nnz, word_luts, (const unsigned char *)d_luts + kLutMaxBytes,
                                        h->d_words, st)) != cudaSuccess ||
@@ -564,50 +672,49 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     double prev = 0.0, fit = 0.0;
     int done = 0;
     int hstatus[3] = {0, 0, 0};
-    for (int it = 1; it <= iters; it++) {
-        for (int n = 0; n < N; n++) {
-            const int64_t In = (int64_t)h->dims[n];
-            // V of mode n (other modes' Grams, all final in stream order) on aux
-            if ((e = cudaEventRecord(h->ev_g, st)) != cudaSuccess ||
-                (e = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess ||
-                (e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
-                                      h->d_status, h->aux)) != cudaSuccess ||
-                (e = cudaEventRecord(h->ev_v, h->aux)) != cudaSuccess)
-                return cuda_fail(e, "relate_cpals: normal equations");
-            rc = run_mttkrp(h, n, factors, R, h->d_M, st);
-            if (rc) return rc;
-            if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess ||
-                (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess)
-                return cuda_fail(e, "relate_cpals: mode update");
-            if (h->factor_dtype == RELATE_BF16 && gram_tc_supported(R)) {
-                // lambda from Ahat's column norms, store the normalised BF16
-                // factor, then its Gram on the tensor cores (of the stored values)
-                if ((e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
-                    (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
-                                            st)) != cudaSuccess ||
-                    (e = launch_gram(factors[n], In, R, RELATE_BF16, h->d_scratch, h->d_G + n * RR, st)) !=
-                        cudaSuccess ||
-                    (e = launch_inner_from_gram(h->d_V, h->d_G + n * RR, h->d_lambda, R, h->d_inner, st)) !=
-                        cudaSuccess)
-                    return cuda_fail(e, "relate_cpals: mode update");
-            } else if ((e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) !=
-                           cudaSuccess ||
-                       (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) !=
-                           cudaSuccess ||
-                       (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
-                                               st)) != cudaSuccess)
-                return cuda_fail(e, "relate_cpals: mode update");
+    if (!h->h_pinned && !(h->h_pinned = g_pinned.get()))
+        return fail(RELATE_ERR_OOM, "relate_cpals: pinned host words");
+    double *p_fit = h->h_pinned;
+    int *p_stat = reinterpret_cast<int *>(h->h_pinned + 1);  // status[0], status[1], err
+    cudaGraphExec_t gexec = nullptr;
+    // the legacy default stream cannot be captured: graph mode needs a stream
+    const bool graph = h->use_graph && st != nullptr && iters > 0;
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: begin capture");
+        rc = cpals_iteration(h, R, factors, p_fit, p_stat);
+        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
         }
-        if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess)
-            return cuda_fail(e, "relate_cpals: fit");
-        if ((e = cudaMemcpyAsync(&fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(hstatus, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(hstatus + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        if (e2 != cudaSuccess) return cuda_fail(e2, "relate_cpals: end capture");
+        e = cudaGraphInstantiate(&gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "relate_cpals: graph instantiate");
+    }
+    for (int it = 1; it <= iters; it++) {
+        if (graph) {
+            if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) {
+                cudaGraphExecDestroy(gexec);
+                return cuda_fail(e, "relate_cpals: graph launch");
+            }
+        } else if ((rc = cpals_iteration(h, R, factors, p_fit, p_stat)) != RELATE_OK) {
+            return rc;
+        }
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            if (gexec) cudaGraphExecDestroy(gexec);
             return cuda_fail(e, "relate_cpals: fit to host");
+        }
+        fit = *p_fit;
+        hstatus[0] = p_stat[0];
+        hstatus[1] = p_stat[1];
+        hstatus[2] = p_stat[2];
         done = it;
         if (info && info->fit_trace) info->fit_trace[it - 1] = fit;
         if (hstatus[2]) {
+            if (gexec) cudaGraphExecDestroy(gexec);
             cudaMemsetAsync(h->d_err, 0, 16, st);
             if (info) {
                 info->fit = fit;
@@ -620,6 +727,7 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
         if (it > 1 && (fit - prev < tol && prev - fit < tol)) break;
         prev = fit;
     }
+    if (gexec) cudaGraphExecDestroy(gexec);
     if ((e = cudaMemcpyAsync(lambda, h->d_lambda, sizeof(double) * R, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals: lambda to host");
@@ -677,6 +785,51 @@ int relate_set_precision(relate_handle_t h, relate_dtype_t factor_dtype, relate_
         return fail(RELATE_ERR_INVALID_ARG, "relate_set_precision: unsupported dtype pair");
     h->factor_dtype = factor_dtype;
     h->acc_dtype = acc_dtype;
+    return RELATE_OK;
+}
+
+int relate_footprint(const uint64_t *dims, int nmodes, int64_t nnz, const relate_params_t *params, int R,
+                     relate_footprint_t *out) {
+    g_err[0] = 0;
+    if (!out || !dims) return fail(RELATE_ERR_INVALID_ARG, "relate_footprint: NULL argument");
+    memset(out, 0, sizeof(*out));
+    relate_params_t defaults;
+    relate_params_default(&defaults);
+    const relate_params_t *p = params ? params : &defaults;
+    if (nmodes < 2 || nmodes > RELATE_MAX_MODES || nnz < 0 || nnz > (int64_t)0xffffffffLL || R < 1 ||
+        R > RELATE_MAX_RANK || p->partition_size < 0 || !valid_precision(p->factor_dtype, p->acc_dtype) ||
+        (p->val_dtype != RELATE_F64 && p->val_dtype != RELATE_F32))
+        return fail(RELATE_ERR_INVALID_ARG, "relate_footprint: bad argument");
+    int lp = 0;
+    uint64_t maxI = 0, sumI = 0;
+    for (int m = 0; m < nmodes; m++) {
+        if (dims[m] < 1 || dims[m] > ((uint64_t)1 << 32))
+            return fail(RELATE_ERR_INVALID_ARG, "relate_footprint: dims[%d] not in [1, 2^32]", m);
+        lp += bits_for(dims[m]);
+        maxI = dims[m] > maxI ? dims[m] : maxI;
+        sumI += dims[m];
+    }
+    if (lp > RELATE_MAX_KEY_BITS) return fail(RELATE_ERR_KEY_TOO_WIDE, "relate_footprint: l(p)=%d > 128", lp);
+    const size_t kb = lp <= 32 ? 4 : lp <= 64 ? 8 : 16;
+    const int vb = p->val_dtype == RELATE_F64 ? 8 : 4;
+    const int64_t S = p->partition_size > 0 ? p->partition_size : 4096;
+    const int64_t P = (nnz + S - 1) / S;
+    const size_t resident = words_bytes(nnz, kb) + vals_bytes(nnz, vb) + 2 * bounds_bytes(P, nmodes) + 64 + 16 +
+                            sumI * 4 + (size_t)nmodes * kHotMax * 4 + perm_bytes(nnz);
+    size_t temps = 2 * (size_t)nnz * kb + 2 * (size_t)nnz * 4 + radix_sort_temp_bytes(nnz) + 64 + kSmallBytes +
+                   2 * (size_t)kLutMaxBytes + hot_table_temp_bytes(maxI);
+    if (!p->coords_on_device && nnz > 0) temps += (size_t)nmodes * nnz * 4 + (size_t)nnz * vb;
+    out->encode_peak = resident + temps;
+    out->resident = resident;
+    out->cpals_workspace = ws_total(maxI, nmodes, R);
+    out->factors = sumI * (uint64_t)R * dtype_bytes(p->factor_dtype);
+    return RELATE_OK;
+}
+
+int relate_set_cpals_graph(relate_handle_t h, int enable) {
+    g_err[0] = 0;
+    if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_set_cpals_graph: NULL handle");
+    h->use_graph = enable ? 1 : 0;
     return RELATE_OK;
 }
 

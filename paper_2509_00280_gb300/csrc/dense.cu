@@ -428,7 +428,7 @@ cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scra
 cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv, float *Vinv32, double *Vsave,
                              int f64_apply, int *status, cudaStream_t st) {
     const size_t smem = 2 * sizeof(double) * MAXR * (MAXR + 1);
-    cudaError_t e = cudaFuncSetAttribute(k_normal_eq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(k_normal_eq);
     if (e != cudaSuccess) return e;
     k_normal_eq<<<1, kThreads, smem, st>>>(G_all, N, n, R, Vinv, Vinv32, Vsave, f64_apply, status);
     return cudaGetLastError();

@@ -581,7 +581,7 @@ cudaError_t rs_passes(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, 
     uint32_t *hist = reinterpret_cast<uint32_t *>(temp);
     uint32_t *sums = hist + hlen;
     const size_t smem = sizeof(K) * RS_TILE + sizeof(uint32_t) * RS_TILE;
-    cudaError_t e = cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(k_rs_scatter<K>);
     if (e != cudaSuccess) return e;
     K *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
@@ -773,7 +773,7 @@ cudaError_t launch_build_keys_lut(int KW, const uint32_t *coords, const uint64_t
     case 1: k_build_keys_lut<1><<<g, kThreads, smem, st>>>(coords, dims_dev, n, N, d, (const unsigned long long *)tables, (uint32_t *)keys, idx, err); break;
     case 2: k_build_keys_lut<2><<<g, kThreads, smem, st>>>(coords, dims_dev, n, N, d, (const unsigned long long *)tables, (unsigned long long *)keys, idx, err); break;
     default: {
-        cudaError_t e = cudaFuncSetAttribute(k_build_keys_lut<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(k_build_keys_lut<4>);
         if (e != cudaSuccess) return e;
         k_build_keys_lut<4><<<g, kThreads, smem, st>>>(coords, dims_dev, n, N, d, (const u128 *)tables, (W128 *)keys, idx, err);
     }
@@ -790,7 +790,7 @@ cudaError_t launch_make_words_lut(int KW, const void *keys, int64_t n, const Byt
     case 1: k_make_words_lut<1><<<g, kThreads, smem, st>>>((const uint32_t *)keys, n, d, (const unsigned long long *)tables, (uint32_t *)words); break;
     case 2: k_make_words_lut<2><<<g, kThreads, smem, st>>>((const unsigned long long *)keys, n, d, (const unsigned long long *)tables, (unsigned long long *)words); break;
     default: {
-        cudaError_t e = cudaFuncSetAttribute(k_make_words_lut<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(k_make_words_lut<4>);
         if (e != cudaSuccess) return e;
         k_make_words_lut<4><<<g, kThreads, smem, st>>>((const W128 *)keys, n, d, (const u128 *)tables, (W128 *)words);
     }

@@ -231,7 +231,7 @@ int gram_tc_blocks(int64_t I) {
 cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err, cudaStream_t st) {
     const int g = gram_tc_blocks(I);
     const size_t smem = 2 * (size_t)TC_STAGE_BYTES;
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(k_gram_tc);
     if (e != cudaSuccess) return e;
     k_gram_tc<<<g, TC_THREADS, smem, st>>>(A, I, R, partial, err);
     return cudaGetLastError();

@@ -18,6 +18,23 @@ constexpr int kMaxModes = RELATE_MAX_MODES;
 constexpr int kMaxRuns = RELATE_MAX_KEY_BITS;
 constexpr int kThreads = 256;  // threads per block of the streaming kernels
 
+// The most dynamic shared memory `kern` can launch with on the current
+// device: the opt-in limit per block minus the kernel's static shared memory
+// (cached per kernel and device); 0 on error.
+int max_dynamic_smem(const void *kern);
+
+// Lets `kern` launch with up to max_dynamic_smem(kern). The limit is a
+// per-function attribute shared by all host threads, so it is always set to
+// that one value, never to a launch's own size: another thread's launch, or a
+// node of a graph it is still capturing, is never left above a limit lowered
+// in between.
+template <typename K>
+cudaError_t allow_max_dynamic_smem(K kern) {
+    const int lim = max_dynamic_smem(reinterpret_cast<const void *>(kern));
+    if (lim <= 0) return cudaErrorInvalidDeviceFunction;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
 // A maximal run of bits that one mode contributes to the position p:
 // bits [src, src+len) of i_mode land in bits [dst, dst+len) of p
 // (Sec. 3.3.1-3.3.2: mode a_t gives its next low bit to b^t, so each mode's

@@ -1,9 +1,35 @@
 // mttkrp.cu -- host-side launch configuration of the MTTKRP kernel:
 // grid sizing in multiples of the SM count, shared-memory accumulators,
 // vector-path eligibility.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "mttkrp_impl.cuh"
 
 namespace relate {
+
+int max_dynamic_smem(const void *kern) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const auto key = std::make_pair(dev, kern);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+        return 0;
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = lim;
+    return lim;
+}
 
 int mttkrp_acc_bytes(int factor_dtype) { return factor_dtype == RELATE_F64 ? 8 : 4; }
 

@@ -565,7 +565,7 @@ cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStre
     }
     const size_t smem = ((acc_bytes + 15) & ~(size_t)15) + tile_bytes<NT, KW, typename Prec<FT>::C>(a.vals_f64 ? 8 : 4);
     auto kern = k_mttkrp<NT, KW, FT, VEC, VPL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, smem, st>>>(a, log2G);
     return cudaGetLastError();

@@ -78,6 +78,8 @@ def lib():
                 "relate_set_conflict": (I, [P, I, I]),
                 "relate_set_precision": (I, [P, I, I]),
                 "relate_set_stream": (I, [P, P]),
+                "relate_set_cpals_graph": (I, [P, I]),
+                "relate_footprint": (I, [P, I, I64, P, I, P]),
                 "relate_decode": (I, [P, P, P, P, P, P]),
                 "relate_get_partitions": (I, [P, P, P, P]),
                 "relate_gram": (I, [P, I64, I, I, P, P]),
@@ -261,6 +263,35 @@ def relate_set_precision(h: Handle, factor_dtype, acc_dtype=None) -> None:
 
 def relate_set_stream(h: Handle, stream) -> None:
     _check(lib().relate_set_stream(h.raw, _stream(stream)), "relate_set_stream")
+
+
+class Footprint(ctypes.Structure):
+    _fields_ = [("encode_peak", ctypes.c_uint64), ("resident", ctypes.c_uint64),
+                ("cpals_workspace", ctypes.c_uint64), ("factors", ctypes.c_uint64)]
+
+
+def relate_footprint(dims, nnz: int, R: int, factor_dtype="f32", val_dtype="f32", partition_size: int = 0,
+                     coords_on_device: bool = False) -> dict:
+    """Device bytes relate_encode / relate_cpals request for this shape (host
+    only). 'peak' = max(encode_peak, resident + cpals_workspace) + factors."""
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.uint64))
+    p = Params()
+    lib().relate_params_default(ctypes.byref(p))
+    p.partition_size = int(partition_size)
+    p.val_dtype = _DTYPES[val_dtype]
+    p.factor_dtype = _DTYPES[factor_dtype]
+    p.acc_dtype = RELATE_F64 if factor_dtype == "f64" else RELATE_F32
+    p.coords_on_device = int(bool(coords_on_device))
+    f = Footprint()
+    _check(lib().relate_footprint(d.ctypes.data, len(d), int(nnz), ctypes.byref(p), int(R), ctypes.byref(f)),
+           "relate_footprint")
+    out = {k: int(getattr(f, k)) for k, _ in Footprint._fields_}
+    out["peak"] = max(out["encode_peak"], out["resident"] + out["cpals_workspace"]) + out["factors"]
+    return out
+
+
+def relate_set_cpals_graph(h: Handle, enable: bool) -> None:
+    _check(lib().relate_set_cpals_graph(h.raw, int(bool(enable))), "relate_set_cpals_graph")
 
 
 def relate_decode(h: Handle, coords_out=None, vals_out=None, perm_out=None, keys_out=None, stream=None) -> None:

@@ -84,6 +84,8 @@ TAG_VAL = 0x200
 TAG_VAL2 = 0x201
 TAG_FACTOR = 0x300
 TAG_LABELS = 0x400  # + mode
+TAG_REQUEST = 0x500
+TAG_ARRIVAL = 0x600
 
 
 def mix64(z: np.ndarray) -> np.ndarray:
@@ -139,7 +141,7 @@ class TensorSpec:
     value_dtype: str = "f32"  # "f32" or "f64"
     seed: int = 1
     shuffle: bool = False
-    distinct: bool = True
+    distinct: bool | str = True   # True, False, or "once" (see make_tensor)
     extra: dict = field(default_factory=dict)
 
 
@@ -308,8 +310,46 @@ def make_values(spec: TensorSpec) -> np.ndarray:
     return v.astype(np.float32) if spec.value_dtype == "f32" else v.astype(np.float64)
 
 
+def _distinct_once(spec: TensorSpec) -> tuple[np.ndarray, np.ndarray]:
+    """Draws spec.nnz tuples once and keeps the first occurrence of each
+    distinct tuple (no top-up): returns (coords, indices of the kept draws)."""
+    N = len(spec.dims)
+    tables = [zipf_table(int(I), d[1]) if d[0] == "zipf" else None for I, d in zip(spec.dims, spec.dists)]
+    if spec.shuffle:
+        tables += [label_permutation(spec.seed, n, int(spec.dims[n])) for n in range(N)]
+    c = _draw_coords(spec, 0, spec.nnz, tables)
+    L = _clib()
+    if L is not None and spec.nnz > 0:
+        dims = np.array(spec.dims, dtype=np.uint64)
+        st = L.synth_dedup_new(N, dims.ctypes.data, _split_point(spec.dims), 2 * spec.nnz + 4096, _threads())
+        if st:
+            try:
+                keep = np.zeros(spec.nnz, dtype=np.uint8)
+                if L.synth_dedup_insert(st, c.ctypes.data, spec.nnz, keep.ctypes.data) >= 0 and not (keep == 2).any():
+                    idx = np.nonzero(keep)[0]
+                    return np.ascontiguousarray(c[:, idx]), idx
+            finally:
+                L.synth_dedup_free(st)
+    keys = _dedup_keys(c, spec.dims)
+    order = np.lexsort(keys[::-1]) if c.shape[1] else np.zeros(0, dtype=np.int64)
+    first = np.ones(c.shape[1], dtype=bool)
+    if c.shape[1] > 1:
+        same = np.ones(c.shape[1] - 1, dtype=bool)
+        for k in keys:
+            ks = k[order]
+            same &= ks[1:] == ks[:-1]
+        first[order[1:][same]] = False  # lexsort is stable: the first draw stays
+    idx = np.nonzero(first)[0]
+    return np.ascontiguousarray(c[:, idx]), idx
+
+
 def make_tensor(spec: TensorSpec):
-    """Returns (coords (N, nnz) uint32 SoA, vals (nnz,) f32/f64)."""
+    """Returns (coords (N, nnz) uint32 SoA, vals (nnz,) f32/f64). With
+    distinct == "once", spec.nnz tuples are drawn once and repeats dropped
+    (the tensor then has at most spec.nnz nonzeros)."""
+    if spec.distinct == "once":
+        c, idx = _distinct_once(spec)
+        return c, make_values(spec)[idx]
     return make_coords(spec), make_values(spec)
 
 
@@ -368,3 +408,40 @@ def scaled(spec: TensorSpec, nnz: int, dims=None, name: str | None = None) -> Te
     """The same recipe at a smaller size (for parity cases)."""
     return TensorSpec(name or f"{spec.name}@{nnz}", tuple(dims or spec.dims), nnz, spec.dists,
                       spec.values, spec.value_dtype, spec.seed, spec.shuffle, spec.distinct)
+
+
+def _log_uniform(u: float, lo: float, hi: float) -> float:
+    return math.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))
+
+
+def _pick(u: float, choices):
+    return choices[min(int(u * len(choices)), len(choices) - 1)]
+
+
+def serving_request(i: int, seed_base: int = 1000, nnz_range=(1e4, 2e7), dim_range=(100, 1e6),
+                    alpha_range=(1.0, 1.4), ranks=(8, 16, 32, 64), modes=(3, 4, 5)):
+    """Request i of the serving mix (the decomposition requests of a
+    CP-ALS service): seed = seed_base + i; N uniform over `modes`; nnz and
+    every I_n log-uniform over their ranges; one Zipf exponent for all modes,
+    uniform over alpha_range; R uniform over `ranks`; U(0,1] FP32 values.
+    nnz tuples are drawn once and repeated tuples dropped (first draw kept),
+    since a Zipf law on 100-long modes cannot supply millions of distinct
+    tuples: the tensor has at most nnz nonzeros. Returns (TensorSpec, R)."""
+    seed = seed_base + int(i)
+    u = uniform01(stream(seed, TAG_REQUEST, np.arange(16, dtype=np.uint64)))
+    N = _pick(u[0], modes)
+    nnz = int(round(_log_uniform(u[1], *nnz_range)))
+    dims = tuple(int(round(_log_uniform(u[2 + n], *dim_range))) for n in range(N))
+    alpha = alpha_range[0] + u[12] * (alpha_range[1] - alpha_range[0])
+    R = _pick(u[13], ranks)
+    spec = TensorSpec(f"serve-{i}", dims, nnz, (("zipf", float(alpha)),) * N, values="uniform",
+                      value_dtype="f32", seed=seed, distinct="once")
+    return spec, R
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson process of the given rate:
+    cumulative sums of exponential gaps -ln(u) / rate."""
+    u = uniform01(stream(seed, TAG_ARRIVAL, np.arange(n, dtype=np.uint64)))
+    return np.cumsum(-np.log(u) / float(rate))
+

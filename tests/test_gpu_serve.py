@@ -1,0 +1,93 @@
+"""The CP-ALS service on the GPU.
+
+* graph replay of an ALS iteration gives the plain path's results;
+* a request served alone and in a concurrent mix gives the same CP model
+  (same kernels; only the order of floating-point atomic additions varies);
+* a served request matches the CPU oracle's CP-ALS from the same initial
+  factors (FP64 within 1e-9, FP32 fit within 1e-3);
+* admission keeps the admitted footprint within a small budget.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2509_00280_gb300 as rl
+from paper_2509_00280_gb300 import serve
+from gpu_util import DEV, encode_dev, factors_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(n, nnz_range=(1e4, 2e5), iters=8):
+    reqs = serve.make_requests(n, nnz_range=nnz_range, tol=0.0, max_iters=iters, return_factors=True)
+    return reqs
+
+
+@pytest.mark.parametrize("fdt", ["f64", "f32", "bf16"])
+def test_graph_replay_matches_plain_path(fdt):
+    spec = synth.scaled(synth.WORKLOADS["zipf3d-200Kx200Kx5K-50M"]["spec"], 300_000, dims=(20000, 20000, 500))
+    c, v = synth.make_tensor(spec)
+    R = 16
+    fs = synth.init_factors(spec.dims, R, seed=0, dtype=np.float32)
+    vals = v.astype(np.float64) if fdt == "f64" else v
+    out = []
+    for graph in (False, True):
+        s = torch.cuda.Stream()
+        h = encode_dev(c, vals, spec.dims, factor_dtype=fdt, stream=s)
+        rl.relate_set_cpals_graph(h, graph)
+        dfs = factors_dev(fs, fdt)
+        torch.cuda.synchronize()
+        res = rl.relate_cpals(h, R, 6, 0.0, dfs)
+        out.append((res, [f.float().cpu().numpy() for f in dfs]))
+        h.close()
+    (a, fa), (b, fb) = out
+    assert a["iters"] == b["iters"] == 6 and b["status"] == 0
+    # atomic-add order differs run to run; in BF16 that can flip the rounding
+    # of a stored factor entry, so BF16 gets its fit acceptance bound (1e-3)
+    tol = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-3}[fdt]
+    assert np.max(np.abs(a["fit_trace"] - b["fit_trace"])) <= tol
+    for x, y in zip(fa, fb):
+        assert np.max(np.abs(x - y)) <= (1e-9 if fdt == "f64" else 2e-2 if fdt == "bf16" else 1e-3)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_alone_and_in_the_mix_agree(prec):
+    reqs = serve.with_precision(_mix(8), prec)
+    alone, _, _ = serve.run_mix(reqs, workers=1)
+    mixed, summ, _ = serve.run_mix(reqs, workers=6)
+    assert summ["requests"] == 8
+    for a, m in zip(alone, mixed):
+        assert a.rid == m.rid and a.iters == m.iters == 8 and a.status == m.status == 0
+        if prec == "f64":
+            assert abs(a.fit - m.fit) <= 1e-9
+            for x, y in zip(a.factors, m.factors):
+                assert np.max(np.abs(x - y)) <= 1e-7
+        else:
+            assert abs(a.fit - m.fit) <= 1e-4
+
+
+def test_served_requests_match_the_oracle():
+    base = _mix(3, nnz_range=(2e4, 6e4), iters=6)
+    for r in base:
+        init = [np.asarray(f.cpu().numpy(), dtype=np.float64)
+                for f in serve.initial_factors(r.dims, r.R, r.init_seed, DEV, torch.float32)]
+        ref = oracle.cpals(r.coords, r.vals.astype(np.float64), r.dims, r.R, 6, 0.0, init)
+        f64, _, _ = serve.run_mix(serve.with_precision([r], "f64"), workers=2)
+        f32, _, _ = serve.run_mix([r], workers=2)
+        assert np.max(np.abs(f64[0].fit_trace - ref["fit_trace"])) <= 1e-9
+        np.testing.assert_allclose(f64[0].lam, ref["lam"], rtol=1e-7)
+        assert abs(f32[0].fit - ref["fit_trace"][-1]) <= 1e-3
+
+
+def test_admission_respects_a_small_budget():
+    reqs = _mix(10, iters=3)
+    fps = [serve.footprint(r) for r in reqs]
+    budget = 2 * max(fps)
+    res, summ, q = serve.run_mix(reqs, workers=8, budget_bytes=budget)
+    assert summ["requests"] == 10 and all(r.status == 0 for r in res)
+    assert q["peak_admitted_bytes"] <= budget and q["admitted"] == 10
+    # the pool's footprint estimate is an upper bound of what the request used
+    free0, _ = torch.cuda.mem_get_info()
+    assert max(fps) < free0
