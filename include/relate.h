@@ -54,14 +54,21 @@ typedef enum { RELATE_F64 = 0, RELATE_F32 = 1, RELATE_BF16 = 2 } relate_dtype_t;
 /* How one mode's MTTKRP resolves writes of many nonzeros to one output row
  * (Sec. 4.1.3: reduction-based vs atomic synchronisation, chosen from the
  * tensor's fiber statistics, Sec. 4.2.1).
- *  ATOMIC     - runs of equal i_n are merged in registers, then added to the
- *               output with global atomics.
- *  SEGMENTED  - the same runs, merged per partition in a shared-memory window
- *               spanning the partition's [lo_n, hi_n] rows, flushed once per
- *               partition (atomics only where a window does not fit).
- *  PRIVATIZED - the whole output (I_n x R) is privatised in shared memory per
- *               thread block and flushed once per block.
- *  AUTO       - chosen per mode from the encode-time statistics. */
+ *  ATOMIC     - tiles keep the encoded order; runs of equal i_n are merged in
+ *               registers and added to the output with global vector atomics,
+ *               except the mode's most populated rows (up to 256), which
+ *               accumulate in shared memory and are flushed once per block.
+ *  SEGMENTED  - every 2048-nonzero tile is first sorted by i_n in shared memory
+ *               (bins = rows of the partition's [lo_n, hi_n] range, or a hash
+ *               of the row when that range is wider than 2048), so each run of
+ *               equal rows is merged in registers and written once per tile.
+ *  PRIVATIZED - sorted tiles as SEGMENTED, and the whole output (I_n x R) is
+ *               privatised in shared memory per thread block and flushed once
+ *               per block (only when it fits; otherwise SEGMENTED runs).
+ *  AUTO       - chosen per mode from the encode-time statistics:
+ *               PRIVATIZED if I_n x R x acc bytes <= 32 KB, else SEGMENTED if
+ *               nnz / distinct(i_n) >= 8 or the mean run of equal i_n >= 8,
+ *               else ATOMIC. */
 typedef enum {
     RELATE_CONFLICT_AUTO = 0,
     RELATE_CONFLICT_ATOMIC = 1,

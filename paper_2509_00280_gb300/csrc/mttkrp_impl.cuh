@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
 
         // ---- block-local counting sort of the tile by output row: bins are
         // rows - lo when the partition's rows span at most kSortBins, else a
-        // 12-bit multiplicative hash of the row (equal rows share a bin, so
+        // 11-bit multiplicative hash of the row (equal rows share a bin, so
         // their nonzeros stay adjacent unless another row hashes alike)
         const uint32_t lo = a.plo[q * N + mode];
         const uint32_t span = a.phi[q * N + mode] - lo + 1;
