@@ -207,7 +207,7 @@ typedef struct {
     uint64_t factors;          /* caller-owned factors: sum_n I_n * R * dtype */
 } relate_footprint_t;
 
-/* Device bytes requested from the stream-ordered allocator by relate_encode
+/* Device bytes requested from the library's stream-ordered pool by relate_encode
  * and relate_cpals for a tensor of this shape, before the allocator's own
  * rounding (a serving layer admits requests by this). A request's peak is
  * max(encode_peak, resident + cpals_workspace) + factors. Host only: makes no
@@ -215,6 +215,13 @@ typedef struct {
  * KEY_TOO_WIDE. */
 int relate_footprint(const uint64_t *dims, int nmodes, int64_t nnz, const relate_params_t *params, int R,
                      relate_footprint_t *out);
+
+/* Returns to the driver the device memory that the library's allocation pool
+ * of the current device keeps cached after handles were freed (the pool keeps
+ * freed blocks mapped so that the next encode or CP-ALS reuses them). Memory
+ * of live handles is untouched. Host call; no synchronisation. The paper has
+ * no counterpart. Errors: CUDA. */
+int relate_release_cached_memory(void);
 
 /* enable != 0: relate_cpals captures one ALS iteration (every mode's MTTKRP,
  * normal equations, solve, Gram and normalisation, the fit, and the copy of

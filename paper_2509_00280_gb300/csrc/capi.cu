@@ -36,6 +36,46 @@ bool valid_precision(int f, int a) {
 
 int dtype_bytes(int d) { return d == RELATE_F64 ? 8 : d == RELATE_F32 ? 4 : 2; }
 
+// Device memory of handles comes from one stream-ordered pool per device,
+// owned by the library. Its release threshold is unlimited: freed blocks stay
+// mapped for the next encode or CP-ALS instead of going back to the driver
+// at every synchronisation (relate_release_cached_memory trims it).
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaError_t lib_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = lib_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, pool, st);
+}
+
 // Device bytes of each allocation. relate_encode, the CP-ALS workspace and
 // relate_footprint all size their buffers from these.
 // 64 bytes of tail padding: tile copies round their size up to 16 bytes
@@ -229,7 +269,7 @@ struct AsyncBufs {
     std::vector<void *> ptrs;
     cudaError_t alloc(void **p, size_t bytes) {
         *p = nullptr;
-        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+        cudaError_t e = dalloc(p, bytes ? bytes : 16, st);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }
@@ -256,16 +296,16 @@ int ensure_ws(relate_handle_s *h, int R) {
     for (int m = 0; m < h->N; m++) maxI = h->dims[m] > maxI ? h->dims[m] : maxI;
     const WsSizes w = ws_sizes(maxI, h->N, R);
     cudaError_t e;
-    if ((e = cudaMallocAsync(&h->d_M, w.M, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_scratch, w.scratch, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_G, w.G, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_Vinv, w.RR8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_V, w.RR8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_Vinv32, w.RR4, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_lambda, w.R8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_inner, w.R8, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_fit, 64, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&h->d_status, 64, st)) != cudaSuccess)
+    if ((e = dalloc(&h->d_M, w.M, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_scratch, w.scratch, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_G, w.G, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_Vinv, w.RR8, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_V, w.RR8, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_Vinv32, w.RR4, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_lambda, w.R8, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_inner, w.R8, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_fit, 64, st)) != cudaSuccess ||
+        (e = dalloc((void **)&h->d_status, 64, st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals workspace");
     if (!h->aux && ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
                     (e = cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
@@ -490,19 +530,19 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
         const size_t sort_bytes = radix_sort_temp_bytes(nnz);
         // persistent encoding arrays
         // 64 bytes of tail padding: tile copies round their size up to 16 bytes
-        if ((e = cudaMallocAsync(&h->d_words, words_bytes(nnz, kb), st)) != cudaSuccess ||
-            (e = cudaMallocAsync(&h->d_vals, vals_bytes(nnz, vb), st)) != cudaSuccess ||
-            (e = cudaMallocAsync((void **)&h->d_plo, bounds_bytes(h->P, N), st)) != cudaSuccess ||
-            (e = cudaMallocAsync((void **)&h->d_phi, bounds_bytes(h->P, N), st)) != cudaSuccess ||
-            (e = cudaMallocAsync((void **)&h->d_normX2, 64, st)) != cudaSuccess ||
-            (e = cudaMallocAsync((void **)&h->d_err, 16, st)) != cudaSuccess ||
+        if ((e = dalloc(&h->d_words, words_bytes(nnz, kb), st)) != cudaSuccess ||
+            (e = dalloc(&h->d_vals, vals_bytes(nnz, vb), st)) != cudaSuccess ||
+            (e = dalloc((void **)&h->d_plo, bounds_bytes(h->P, N), st)) != cudaSuccess ||
+            (e = dalloc((void **)&h->d_phi, bounds_bytes(h->P, N), st)) != cudaSuccess ||
+            (e = dalloc((void **)&h->d_normX2, 64, st)) != cudaSuccess ||
+            (e = dalloc((void **)&h->d_err, 16, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(h->d_err, 0, 16, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: allocation");
             goto done;
         }
         for (int m = 0; m < N; m++)
-            if ((e = cudaMallocAsync((void **)&h->d_counts[m], h->dims[m] * 4, st)) != cudaSuccess ||
-                (e = cudaMallocAsync((void **)&h->d_hot_rows[m], kHotMax * 4, st)) != cudaSuccess) {
+            if ((e = dalloc((void **)&h->d_counts[m], h->dims[m] * 4, st)) != cudaSuccess ||
+                (e = dalloc((void **)&h->d_hot_rows[m], kHotMax * 4, st)) != cudaSuccess) {
                 rc = cuda_fail(e, "relate_encode: allocation");
                 goto done;
             }
@@ -567,7 +607,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
         }
         void *skeys = in_alt ? keys_alt : keys;
         uint32_t *sperm = (uint32_t *)(in_alt ? idx_alt : idx);
-        if ((e = cudaMallocAsync((void **)&h->d_perm, perm_bytes(nnz), st)) != cudaSuccess ||
+        if ((e = dalloc((void **)&h->d_perm, perm_bytes(nnz), st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(h->d_perm, sperm, nnz * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
             (e = launch_make_words_lut(h->KW, skeys, nnz, word_luts, (const unsigned char *)d_luts + kLutMaxBytes,
                                        h->d_words, st)) != cudaSuccess ||
@@ -826,6 +866,14 @@ int relate_footprint(const uint64_t *dims, int nmodes, int64_t nnz, const relate
     return RELATE_OK;
 }
 
+int relate_release_cached_memory(void) {
+    g_err[0] = 0;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = lib_pool(&pool);
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    return e == cudaSuccess ? RELATE_OK : cuda_fail(e, "relate_release_cached_memory");
+}
+
 int relate_set_cpals_graph(relate_handle_t h, int enable) {
     g_err[0] = 0;
     if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_set_cpals_graph: NULL handle");
@@ -879,7 +927,7 @@ int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G
         return fail(RELATE_ERR_INVALID_ARG, "relate_gram: bad argument");
     const cudaStream_t st = (cudaStream_t)stream;
     void *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, dense_scratch_doubles(R) * 8, st);
+    cudaError_t e = dalloc(&scratch, dense_scratch_doubles(R) * 8, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_gram: scratch");
     e = launch_gram(A, I, R, dtype, (double *)scratch, G, st);
     cudaError_t e2 = cudaFreeAsync(scratch, st);

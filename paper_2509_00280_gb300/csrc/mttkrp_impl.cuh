@@ -115,6 +115,43 @@ template <typename FT> struct VecLoad<FT, 1> {
     }
 };
 
+// Load of VEC consecutive elements of a factor row at p (16-byte aligned for
+// the vector forms), converted to C.
+template <typename FT, int VEC> struct VecLoadP;
+template <> struct VecLoadP<double, 2> {
+    static __device__ __forceinline__ void run(const void *p, double (&x)[2]) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        x[0] = v.x;
+        x[1] = v.y;
+    }
+};
+template <> struct VecLoadP<float, 4> {
+    static __device__ __forceinline__ void run(const void *p, float (&x)[4]) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
+    }
+};
+template <> struct VecLoadP<__nv_bfloat16, 4> {
+    static __device__ __forceinline__ void run(const void *p, float (&x)[4]) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+        x[0] = __uint_as_float(u.x << 16);
+        x[1] = __uint_as_float(u.x & 0xffff0000u);
+        x[2] = __uint_as_float(u.y << 16);
+        x[3] = __uint_as_float(u.y & 0xffff0000u);
+    }
+};
+template <typename FT> struct VecLoadP<FT, 1> {
+    using C = typename Prec<FT>::C;
+    static __device__ __forceinline__ void run(const void *p, C (&x)[1]) { x[0] = (C)*reinterpret_cast<const FT *>(p); }
+};
+
+template <bool B> struct Tail {
+    static constexpr bool value = B;
+};
+
 // global accumulation of one vector (VEC elements) at out + off
 template <typename C, int VEC> struct GAdd;
 template <> struct GAdd<float, 4> {
@@ -211,12 +248,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-template <int NT, int KW, typename FT, int VEC, int VPL>
+// SEG = true: the SEGMENTED strategy without hot rows, fixed at compile time
+// (sorted tiles, every run flushed to global memory), so the flush and the
+// record build carry no strategy branches.
+template <int NT, int KW, typename FT, int VEC, int VPL, bool SEG>
 __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, const int log2G) {
     using C = typename Prec<FT>::C;
     using Word = typename WordT<KW>::T;
     using R_t = Rec<NT, C>;
     constexpr int RB = RecStride<NT, C>::B;
+    static_assert(sizeof(R_t) == RB, "records are indexed as an array of R_t");
     constexpr int U = Unroll<FT, VPL>::U;
     constexpr int NI = R_t::NI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -234,9 +275,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
     const uint32_t mmask = a.fields.mask[mode];
     C *__restrict__ out = reinterpret_cast<C *>(a.out);
     const int strat = a.strategy;
-    const bool priv = strat == RELATE_CONFLICT_PRIVATIZED;
-    const bool sort_tiles = strat != RELATE_CONFLICT_ATOMIC;
-    const int hot_n = priv ? 0 : a.hot_n;
+    const bool priv = !SEG && strat == RELATE_CONFLICT_PRIVATIZED;
+    const bool sort_tiles = SEG || strat != RELATE_CONFLICT_ATOMIC;
+    const int hot_n = (SEG || priv) ? 0 : a.hot_n;
     const int vb = a.vals_f64 ? 8 : 4;
 
     // shared layout: accumulators | raw words | raw values | records | hot slots | row counters | mbarrier
@@ -480,23 +521,31 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
             }
         };
 
-        for (int p0 = jb; p0 < je; p0 += U) {
+        // byte offset of this lane's first vector in a row; a row's address is
+        // one 32 x 32 -> 64-bit multiply-add off the factor's base
+        const uint32_t loff = (uint32_t)gl * VEC * (uint32_t)sizeof(FT);
+        const uint32_t rbytes = (uint32_t)R * (uint32_t)sizeof(FT);
+        const R_t *recs = reinterpret_cast<const R_t *>(srec);
+        // U nonzeros per step; the tail step (fewer than U left) clamps its
+        // record reads and skips the missing nonzeros
+        auto step = [&](int p0, auto tail) {
+            constexpr bool TAIL = decltype(tail)::value;
             R_t rec[U];
             C t[U][VPL][VEC];
 #pragma unroll
-            for (int u = 0; u < U; u++) rec[u] = *reinterpret_cast<const R_t *>(srec + (size_t)min(p0 + u, je - 1) * RB);
+            for (int u = 0; u < U; u++) rec[u] = recs[TAIL ? min(p0 + u, je - 1) : p0 + u];
             bool first = true;
 #pragma unroll
             for (int k = 1; k < NI; k++) {  // record slots 1..N-1: the other modes
                 if (k >= N) continue;
-                const FT *__restrict__ Ak = reinterpret_cast<const FT *>(a.rfac[k]);
                 C x[U][VPL][VEC];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const FT *rowp = Ak + (int64_t)rec[u].idx[k] * R;
+                    const char *rowp = reinterpret_cast<const char *>(a.rfac[k]) +
+                                       ((uint64_t)rec[u].idx[k] * rbytes + loff);
 #pragma unroll
                     for (int v = 0; v < VPL; v++)
-                        if (act[v]) VecLoad<FT, VEC>::run(rowp, vj[v], x[u][v]);
+                        if (act[v]) VecLoadP<FT, VEC>::run(rowp + (size_t)v * G * VEC * sizeof(FT), x[u][v]);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++)
@@ -516,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                if (p0 + u >= je) continue;
+                if (TAIL && p0 + u >= je) continue;
                 const uint32_t row = rec[u].idx[0];
                 const C val = rec[u].val;
                 if (row != cur) {
@@ -533,7 +582,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
                         for (int i = 0; i < VEC; i++) acc[v][i] = fma(val, t[u][v][i], acc[v][i]);
                 }
             }
-        }
+        };
+        for (int p0 = jb; p0 < je; p0 += U) step(p0, Tail<true>{});
         if (cur != 0xffffffffu) flush(cur);
     }
 
@@ -555,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
 }
 
 // Chooses lanes per group for R and launches one instantiation.
-template <int NT, int KW, typename FT, int VEC, int VPL>
+template <int NT, int KW, typename FT, int VEC, int VPL, bool SEG = false>
 cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStream_t st) {
     const int nvec = (a.R + VEC - 1) / VEC;
     int G = 1, log2G = 0;
@@ -564,7 +614,7 @@ cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStre
         log2G++;
     }
     const size_t smem = ((acc_bytes + 15) & ~(size_t)15) + tile_bytes<NT, KW, typename Prec<FT>::C>(a.vals_f64 ? 8 : 4);
-    auto kern = k_mttkrp<NT, KW, FT, VEC, VPL>;
+    auto kern = k_mttkrp<NT, KW, FT, VEC, VPL, SEG>;
     cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, smem, st>>>(a, log2G);
@@ -575,10 +625,12 @@ cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStre
 template <typename FT>
 cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st) {
     constexpr int V = Prec<FT>::VEC;
-#define RELATE_MK_KW(NT_)                                                                        \
-    (KW == 1 ? launch_one<NT_, 1, FT, V, 1>(a, acc_bytes, grid, st)                              \
-             : KW == 2 ? launch_one<NT_, 2, FT, V, 1>(a, acc_bytes, grid, st)                    \
-                       : launch_one<NT_, 4, FT, V, 1>(a, acc_bytes, grid, st))
+#define RELATE_MK_KW_S(NT_, S_)                                                                  \
+    (KW == 1 ? launch_one<NT_, 1, FT, V, 1, S_>(a, acc_bytes, grid, st)                          \
+             : KW == 2 ? launch_one<NT_, 2, FT, V, 1, S_>(a, acc_bytes, grid, st)                \
+                       : launch_one<NT_, 4, FT, V, 1, S_>(a, acc_bytes, grid, st))
+#define RELATE_MK_KW(NT_) (seg ? RELATE_MK_KW_S(NT_, true) : RELATE_MK_KW_S(NT_, false))
+    const bool seg = a.strategy == RELATE_CONFLICT_SEGMENTED && a.hot_n == 0;
     if (!vec_ok) {
         return KW == 1 ? launch_one<0, 1, FT, 1, 2>(a, acc_bytes, grid, st)
                        : KW == 2 ? launch_one<0, 2, FT, 1, 2>(a, acc_bytes, grid, st)
@@ -589,9 +641,10 @@ cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_byt
     case 3: return RELATE_MK_KW(3);
     case 4: return RELATE_MK_KW(4);
     case 5: return RELATE_MK_KW(5);
-    default: return RELATE_MK_KW(0);
+    default: return RELATE_MK_KW_S(0, false);
     }
 #undef RELATE_MK_KW
+#undef RELATE_MK_KW_S
 }
 
 // Per-tile shared bytes of the instantiation a launch will use.

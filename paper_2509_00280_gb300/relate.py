@@ -80,6 +80,7 @@ def lib():
                 "relate_set_stream": (I, [P, P]),
                 "relate_set_cpals_graph": (I, [P, I]),
                 "relate_footprint": (I, [P, I, I64, P, I, P]),
+                "relate_release_cached_memory": (I, []),
                 "relate_decode": (I, [P, P, P, P, P, P]),
                 "relate_get_partitions": (I, [P, P, P, P]),
                 "relate_gram": (I, [P, I64, I, I, P, P]),
@@ -288,6 +289,11 @@ def relate_footprint(dims, nnz: int, R: int, factor_dtype="f32", val_dtype="f32"
     out = {k: int(getattr(f, k)) for k, _ in Footprint._fields_}
     out["peak"] = max(out["encode_peak"], out["resident"] + out["cpals_workspace"]) + out["factors"]
     return out
+
+
+def relate_release_cached_memory() -> None:
+    """Trims the library's device-memory pool of the current device."""
+    _check(lib().relate_release_cached_memory(), "relate_release_cached_memory")
 
 
 def relate_set_cpals_graph(h: Handle, enable: bool) -> None:
