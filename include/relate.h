@@ -139,7 +139,10 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
  * by this call). R in [1, 64]. Asynchronous on `stream`; never synchronises.
  * Factor rows are read with 16-byte vector loads when every factor pointer
  * is 16-byte aligned and R * sizeof(factor) is a multiple of 16; otherwise
- * a scalar path runs. Errors: INVALID_ARG, CUDA (launch failure). */
+ * a scalar path runs. Calls on one handle must be ordered (one stream, or
+ * events): the SEGMENTED strategy keeps per-block copies of a skewed mode's
+ * hottest rows in scratch owned by the handle. Errors: INVALID_ARG, CUDA
+ * (launch failure). */
 int relate_mttkrp(relate_handle_t h, int mode, void *const *factors, int R, void *out,
                   void *stream);
 

@@ -159,6 +159,7 @@ struct relate_handle_s {
     uint32_t *d_plo = nullptr, *d_phi = nullptr;
     uint32_t *d_counts[kMaxModes] = {};
     uint32_t *d_hot_rows[kMaxModes] = {};
+    void *d_hot_scratch = nullptr;  // per-block copies of hot rows (SEGMENTED MTTKRP)
     double *d_normX2 = nullptr;
     int *d_err = nullptr;  // device error flags of this handle's kernels
     uint64_t runs_n[kMaxModes] = {}, distinct[kMaxModes] = {}, maxcount[kMaxModes] = {};
@@ -191,7 +192,7 @@ struct relate_handle_s {
         if (ev_v) cudaEventDestroy(ev_v);
         if (h_pinned) g_pinned.put(h_pinned);
         void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_err, d_M, d_scratch, d_G, d_Vinv,
-                        d_lambda, d_inner, d_fit, d_Vinv32, d_status, d_V};
+                        d_lambda, d_inner, d_fit, d_Vinv32, d_status, d_V, d_hot_scratch};
         for (void *p : ptrs)
             if (p) cudaFreeAsync(p, stream);
         for (auto *p : d_counts)
@@ -332,6 +333,8 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
     a.plo = h->d_plo;
     a.phi = h->d_phi;
     a.hot_rows = h->d_hot_rows[mode];
+    a.maxcount = h->maxcount[mode];
+    a.hot_scratch = h->d_hot_scratch;
     a.err = h->d_err;
     a.strategy = resolve_conflict(h, mode, R);
     const int accb = mttkrp_acc_bytes(h->factor_dtype);
@@ -349,21 +352,32 @@ int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_f
     const int N = h->N;
     const int RR = R * R;
     cudaError_t e;
+    const bool tc_path = h->factor_dtype == RELATE_BF16 && gram_tc_supported(R);
+    // V of mode m (the other modes' Grams) on aux, forked from `st` once the
+    // Grams it reads are final: for mode 0 at the start of the iteration; for
+    // the later modes of the FP32/FP64 path right after the previous mode's
+    // normalised Gram, so that it overlaps that mode's factor store and this
+    // mode's MTTKRP (the BF16 path forms the Gram from the stored factor, so
+    // it forks at the start of the mode)
+    auto fork_normal_eq = [&](int m) -> cudaError_t {
+        cudaError_t x;
+        if ((x = cudaEventRecord(h->ev_g, st)) != cudaSuccess ||
+            (x = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess ||
+            (x = launch_normal_eq(h->d_G, N, m, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
+                                  h->d_status, h->aux)) != cudaSuccess)
+            return x;
+        return cudaEventRecord(h->ev_v, h->aux);
+    };
     for (int n = 0; n < N; n++) {
         const int64_t In = (int64_t)h->dims[n];
-        // V of mode n (other modes' Grams, all final in stream order) on aux
-        if ((e = cudaEventRecord(h->ev_g, st)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess ||
-            (e = launch_normal_eq(h->d_G, N, n, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
-                                  h->d_status, h->aux)) != cudaSuccess ||
-            (e = cudaEventRecord(h->ev_v, h->aux)) != cudaSuccess)
+        if ((n == 0 || tc_path) && (e = fork_normal_eq(n)) != cudaSuccess)
             return cuda_fail(e, "relate_cpals: normal equations");
         int rc = run_mttkrp(h, n, factors, R, h->d_M, st);
         if (rc) return rc;
         if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess ||
             (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess)
             return cuda_fail(e, "relate_cpals: mode update");
-        if (h->factor_dtype == RELATE_BF16 && gram_tc_supported(R)) {
+        if (tc_path) {
             // lambda from Ahat's column norms, store the normalised BF16
             // factor, then its Gram on the tensor cores (of the stored values)
             if ((e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
@@ -374,13 +388,19 @@ int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_f
                 (e = launch_inner_from_gram(h->d_V, h->d_G + n * RR, h->d_lambda, R, h->d_inner, st)) !=
                     cudaSuccess)
                 return cuda_fail(e, "relate_cpals: mode update");
-        } else if ((e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) !=
-                       cudaSuccess ||
-                   (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) !=
-                       cudaSuccess ||
-                   (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
-                                           st)) != cudaSuccess)
-            return cuda_fail(e, "relate_cpals: mode update");
+        } else {
+            // solve, Gram and finish have consumed V^{-1} and V: the next
+            // mode's normal equations may overwrite them from here on
+            if ((e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) !=
+                    cudaSuccess ||
+                (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess)
+                return cuda_fail(e, "relate_cpals: mode update");
+            if (n + 1 < N && (e = fork_normal_eq(n + 1)) != cudaSuccess)
+                return cuda_fail(e, "relate_cpals: normal equations");
+            if ((e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
+                                        st)) != cudaSuccess)
+                return cuda_fail(e, "relate_cpals: mode update");
+        }
     }
     if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(p_fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
@@ -535,6 +555,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
             (e = dalloc((void **)&h->d_plo, bounds_bytes(h->P, N), st)) != cudaSuccess ||
             (e = dalloc((void **)&h->d_phi, bounds_bytes(h->P, N), st)) != cudaSuccess ||
             (e = dalloc((void **)&h->d_normX2, 64, st)) != cudaSuccess ||
+            (e = dalloc(&h->d_hot_scratch, kHotScratchBytes, st)) != cudaSuccess ||
             (e = dalloc((void **)&h->d_err, 16, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(h->d_err, 0, 16, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: allocation");
@@ -855,6 +876,7 @@ int relate_footprint(const uint64_t *dims, int nmodes, int64_t nnz, const relate
     const int64_t S = p->partition_size > 0 ? p->partition_size : 4096;
     const int64_t P = (nnz + S - 1) / S;
     const size_t resident = words_bytes(nnz, kb) + vals_bytes(nnz, vb) + 2 * bounds_bytes(P, nmodes) + 64 + 16 +
+                            kHotScratchBytes +
                             sumI * 4 + (size_t)nmodes * kHotMax * 4 + perm_bytes(nnz);
     size_t temps = 2 * (size_t)nnz * kb + 2 * (size_t)nnz * 4 + radix_sort_temp_bytes(nnz) + 64 + kSmallBytes +
                    2 * (size_t)kLutMaxBytes + hot_table_temp_bytes(maxI);

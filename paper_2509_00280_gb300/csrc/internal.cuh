@@ -157,6 +157,8 @@ struct MttkrpArgs {
     const uint32_t *phi;
     const uint32_t *hot_rows;  // kHotMax rows of the mode, most populated first (0xffffffff = unused)
     int hot_n;                 // hot rows cached in shared memory by this launch
+    uint64_t maxcount;         // nonzeros of the mode's most populated row
+    void *hot_scratch;         // SEGMENTED: per-block copies of the hot rows (kHotScratchBytes)
     int vals_f64;              // values stored as FP64 (else FP32)
     int *err;                  // device flag: bit 0 = a bounded wait timed out
     // record slot j of a decoded nonzero: slot 0 = the output mode, slots
@@ -168,6 +170,10 @@ struct MttkrpArgs {
 
 // Upper bound of hot (most populated) rows per mode kept in shared memory.
 constexpr int kHotMax = 256;
+// Global scratch of a handle for the SEGMENTED kernel's per-block copies of
+// the hot rows: 4 KB per block for up to 1024 blocks.
+constexpr size_t kHotBlockBytes = 4096;
+constexpr size_t kHotScratchBytes = 1024 * kHotBlockBytes;
 
 // Hot rows of one mode from its histogram: the kHotMax most populated rows
 // (ties by row id), most populated first; 0xffffffff pads modes with fewer

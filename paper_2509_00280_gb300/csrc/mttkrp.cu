@@ -31,6 +31,12 @@ int max_dynamic_smem(const void *kern) {
     return lim;
 }
 
+// A SEGMENTED mode caches its hottest rows once its most populated row has
+// this many nonzeros (about one global FP32 addition per tile holding the
+// row): the random walk of 2^15 roundings, 2^-24 * sqrt(2^15) relative, stays
+// well below 1e-5.
+constexpr uint64_t kSegHotMinCount = 1u << 15;
+
 int mttkrp_acc_bytes(int factor_dtype) { return factor_dtype == RELATE_F64 ? 8 : 4; }
 
 cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int val_dtype, int smem_budget,
@@ -79,12 +85,22 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
         // Sorted tiles (SEGMENTED) merge each row's run in registers first,
         // so their flushes go straight to global memory. Runs are tagged
         // 0x80000000|slot, so the hot path needs rows < 2^31.
-        int hot = (a.strategy == RELATE_CONFLICT_ATOMIC && a.hot_rows && a.In < (1ull << 31))
-                      ? (16 * 1024) / (a.R * accb) : 0;
+        // SEGMENTED tiles keep their hottest rows in per-block copies in
+        // global scratch (4 KB per block, no shared memory), and only in modes
+        // whose hottest row has enough nonzeros for its global additions to
+        // matter.
+        int hot = 0;
+        if (a.hot_rows && a.In < (1ull << 31)) {
+            if (a.strategy == RELATE_CONFLICT_ATOMIC)
+                hot = (16 * 1024) / (a.R * accb);
+            else if (a.strategy == RELATE_CONFLICT_SEGMENTED && a.maxcount >= kSegHotMinCount && a.hot_scratch &&
+                     vec_ok && a.N >= 2 && a.N <= 5)
+                hot = (int)(kHotBlockBytes / ((size_t)a.R * accb));
+        }
         if (hot > kHotMax) hot = kHotMax;
         if ((uint64_t)hot > a.In) hot = (int)a.In;
         a.hot_n = hot;
-        acc_bytes = (size_t)hot * a.R * accb;
+        acc_bytes = a.strategy == RELATE_CONFLICT_ATOMIC ? (size_t)hot * a.R * accb : 0;
     }
     const size_t smem = acc_bytes + 16 + tile;
     int per_sm = (int)((227 * 1024) / (smem + 1024));
@@ -94,6 +110,8 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
+    if (a.strategy == RELATE_CONFLICT_SEGMENTED && a.hot_n && (size_t)grid * kHotBlockBytes > kHotScratchBytes)
+        a.hot_n = 0;  // more blocks than scratch copies (over 1024): no hot copies
     switch (factor_dtype) {
     case RELATE_F64: return mttkrp_f64(a, KW, vec_ok, acc_bytes, (int)grid, st);
     case RELATE_F32: return mttkrp_f32(a, KW, vec_ok, acc_bytes, (int)grid, st);

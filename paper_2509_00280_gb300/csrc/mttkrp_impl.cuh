@@ -248,9 +248,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-// SEG = true: the SEGMENTED strategy without hot rows, fixed at compile time
-// (sorted tiles, every run flushed to global memory), so the flush and the
-// record build carry no strategy branches.
+// SEG = true: the SEGMENTED strategy fixed at compile time (sorted tiles, no
+// privatised output), so the flush and the record build carry no strategy
+// branches. Runs go to global memory. Runs of the mode's hottest rows (hot_n >
+// 0, tagged when the records are built) go to the block's own copy of those
+// rows in global scratch (a.hot_scratch, zeroed by the block, same vector
+// atomics), which the block adds into the output once at its end: a row
+// present in tens of thousands of tiles would otherwise take one FP32 global
+// addition per tile, and the rounding of that many additions to one large sum
+// exceeds the FP32 tolerance.
 template <int NT, int KW, typename FT, int VEC, int VPL, bool SEG>
 __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, const int log2G) {
     using C = typename Prec<FT>::C;
@@ -277,11 +283,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
     const int strat = a.strategy;
     const bool priv = !SEG && strat == RELATE_CONFLICT_PRIVATIZED;
     const bool sort_tiles = SEG || strat != RELATE_CONFLICT_ATOMIC;
-    const int hot_n = (SEG || priv) ? 0 : a.hot_n;
+    const int hot_n = priv ? 0 : a.hot_n;
     const int vb = a.vals_f64 ? 8 : 4;
 
     // shared layout: accumulators | raw words | raw values | records | hot slots | row counters | mbarrier
-    const int64_t acc_elems = priv ? (int64_t)a.In * R : (int64_t)hot_n * R;
+    const int64_t acc_elems = priv ? (int64_t)a.In * R : SEG ? 0 : (int64_t)hot_n * R;
+    // SEG: this block's copy of the hot rows in global scratch
+    C *__restrict__ hrep = SEG && hot_n ? reinterpret_cast<C *>(a.hot_scratch) + (int64_t)blockIdx.x * hot_n * R
+                                        : nullptr;
     C *sacc = reinterpret_cast<C *>(smem_raw);
     unsigned char *tarea = smem_raw + ((acc_elems * (int64_t)sizeof(C) + 15) & ~(int64_t)15);
     Word *sw = reinterpret_cast<Word *>(tarea);
@@ -301,6 +310,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
         act[v] = vj[v] < nvec;
     }
     for (int64_t i = threadIdx.x; i < acc_elems; i += kThreads) sacc[i] = C(0);
+    if (SEG && hot_n)  // ordered before this block's atomics by the barriers that follow
+        for (int i = threadIdx.x; i < hot_n * R; i += kThreads) hrep[i] = C(0);
     if (hot_n) {  // hash set of this mode's hot rows (most populated first)
         for (int i = threadIdx.x; i < kHotHash; i += kThreads) hkey[i] = 0xffffffffu;
         __syncthreads();
@@ -442,7 +453,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
                 for (int w = 0; w < (threadIdx.x >> 5); w++) run += wsum[w];
 #pragma unroll
                 for (int i = 0; i < PER; i++) {
-                    if (base + i < (int)nb) bins[base + i] = run;
+                    if (base + i < (int)nb) {
+                        // a direct bin is a single row: a hot row's slot + 1
+                        // rides in bits 16..24 (offsets stay below 2^16), so
+                        // each row of the tile is looked up once
+                        uint32_t bv = run;
+                        if (hot_n && direct && loc[i]) {
+                            const uint32_t hs = hot_slot_of(lo + (uint32_t)(base + i));
+                            if (hs != 0xffffffffu) bv |= (hs + 1u) << 16;
+                        }
+                        bins[base + i] = bv;
+                    }
                     run += loc[i];
                 }
             }
@@ -454,15 +475,24 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
             const int j = i * kThreads + threadIdx.x;
             if (j >= nt) continue;
             const Word w = sw[j];
-            const uint32_t p = sorted ? bins[ibin[i]] + ioff[i] : (uint32_t)j;
+            uint32_t p = (uint32_t)j, hbin = 0;
+            if (sorted) {
+                const uint32_t bv = bins[ibin[i]];
+                p = (bv & 0xffffu) + ioff[i];
+                hbin = bv >> 16;
+            }
             R_t rec;
             rec.val = a.vals_f64 ? (C)reinterpret_cast<const double *>(sv)[j]
                                  : (C)reinterpret_cast<const float *>(sv)[j];
 #pragma unroll
             for (int k = 0; k < NI; k++) rec.idx[k] = k < N ? fld(w, a.rshift[k], a.rmask[k]) : 0u;
             if (hot_n) {  // slot 0 becomes the run's destination: 0x80000000|slot for a hot row
-                const uint32_t hs = hot_slot_of(rec.idx[0]);
-                if (hs != 0xffffffffu) rec.idx[0] = 0x80000000u | hs;
+                if (sorted && direct) {
+                    if (hbin) rec.idx[0] = 0x80000000u | (hbin - 1u);
+                } else {
+                    const uint32_t hs = hot_slot_of(rec.idx[0]);
+                    if (hs != 0xffffffffu) rec.idx[0] = 0x80000000u | hs;
+                }
             }
             *reinterpret_cast<R_t *>(srec + (size_t)p * RB) = rec;
         }
@@ -495,7 +525,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
         auto flush = [&](uint32_t row) {
             C *dst;
             bool shared_acc = true;
-            if (priv) {
+            if (SEG) {
+                shared_acc = false;
+                dst = (hot_n && (row & 0x80000000u)) ? hrep + (int64_t)(row & 0x7fffffffu) * R  // block's copy
+                                                     : out + (int64_t)row * R;
+            } else if (priv) {
                 dst = sacc + (int64_t)row * R;
             } else if (row & 0x80000000u) {  // hot row: its shared-memory slot
                 dst = sacc + (int64_t)(row & 0x7fffffffu) * R;
@@ -596,8 +630,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
         }
     } else if (hot_n) {
         const int tot = hot_n * R;
+        if (SEG) __threadfence();  // this block's atomics on its copy are complete
+        __syncthreads();
         for (int i = threadIdx.x; i < tot; i += kThreads) {
-            const C s = sacc[i];
+            const C s = SEG ? __ldcg(hrep + i) : sacc[i];
             const uint32_t row = __ldg(a.hot_rows + i / R);
             if (s != C(0) && row != 0xffffffffu) atomicAdd(out + (int64_t)row * R + i % R, s);
         }
@@ -630,7 +666,7 @@ cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_byt
              : KW == 2 ? launch_one<NT_, 2, FT, V, 1, S_>(a, acc_bytes, grid, st)                \
                        : launch_one<NT_, 4, FT, V, 1, S_>(a, acc_bytes, grid, st))
 #define RELATE_MK_KW(NT_) (seg ? RELATE_MK_KW_S(NT_, true) : RELATE_MK_KW_S(NT_, false))
-    const bool seg = a.strategy == RELATE_CONFLICT_SEGMENTED && a.hot_n == 0;
+    const bool seg = a.strategy == RELATE_CONFLICT_SEGMENTED;
     if (!vec_ok) {
         return KW == 1 ? launch_one<0, 1, FT, 1, 2>(a, acc_bytes, grid, st)
                        : KW == 2 ? launch_one<0, 2, FT, 1, 2>(a, acc_bytes, grid, st)
