@@ -39,9 +39,10 @@ CPU_SAMPLE_NNZ = 5_000_000  # nonzeros of the workload the CPU oracle runs per s
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": "b942ea4c99b235fefe88b6d6f007041870d66bbcc457d41e649c84716381422e",
-               # 20M-nonzero capture, stream part scaled to 50M nonzeros
-               "bytes_per_launch": 655.9e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
+NCU_TRAFFIC = {"sha256": "adafd1b5e836d5d144442838d6a20caf80766c98907fe88038e79a787ec821f3",
+               # 20M-nonzero capture (296.3 MB per launch), stream part scaled
+               # to 50M nonzeros: 296.3 MB + 30M x 12 B
+               "bytes_per_launch": 656.3e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
 
 
 def _peaks():
@@ -54,9 +55,12 @@ def _peaks():
 
 
 def _kernel_sha() -> str:
-    p = os.path.join(ROOT, "paper_2509_00280_gb300", "csrc", "mttkrp_impl.cuh")
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    """sha256 over the MTTKRP kernel source and its launch configuration."""
+    h = hashlib.sha256()
+    for name in ("mttkrp_impl.cuh", "mttkrp.cu"):
+        with open(os.path.join(ROOT, "paper_2509_00280_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 class ClockSampler:
