@@ -212,7 +212,9 @@ typedef struct {
 
 /* Device bytes requested from the library's stream-ordered pool by relate_encode
  * and relate_cpals for a tensor of this shape, before the allocator's own
- * rounding (a serving layer admits requests by this). A request's peak is
+ * rounding (a serving layer admits requests by this); `resident` counts the
+ * per-mode tile orders (2 bytes per nonzero and mode) that the first MTTKRP
+ * of a SEGMENTED mode adds. A request's peak is
  * max(encode_peak, resident + cpals_workspace) + factors. Host only: makes no
  * CUDA call, needs no GPU. The paper has no counterpart. Errors: INVALID_ARG,
  * KEY_TOO_WIDE. */

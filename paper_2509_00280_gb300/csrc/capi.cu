@@ -83,6 +83,7 @@ size_t words_bytes(int64_t nnz, size_t kb) { return (size_t)nnz * kb + 64; }
 size_t vals_bytes(int64_t nnz, int vb) { return (size_t)nnz * vb + 64; }
 size_t bounds_bytes(int64_t P, int N) { return (size_t)(P + 1) * N * 4; }
 size_t perm_bytes(int64_t nnz) { return (size_t)nnz * 4 + 16; }
+size_t tperm_bytes(int64_t nnz) { return (size_t)nnz * 2 + 64; }
 constexpr size_t kSmallBytes = 8 * (1 + 3 * kMaxModes) + 1024 * 8;
 
 struct WsSizes {
@@ -160,6 +161,7 @@ struct relate_handle_s {
     uint32_t *d_counts[kMaxModes] = {};
     uint32_t *d_hot_rows[kMaxModes] = {};
     void *d_hot_scratch = nullptr;  // per-block copies of hot rows (SEGMENTED MTTKRP)
+    uint16_t *d_tperm[kMaxModes] = {};  // per-mode tile order (SEGMENTED MTTKRP), built on first use
     double *d_normX2 = nullptr;
     int *d_err = nullptr;  // device error flags of this handle's kernels
     uint64_t runs_n[kMaxModes] = {}, distinct[kMaxModes] = {}, maxcount[kMaxModes] = {};
@@ -198,6 +200,8 @@ struct relate_handle_s {
         for (auto *p : d_counts)
             if (p) cudaFreeAsync(p, stream);
         for (auto *p : d_hot_rows)
+            if (p) cudaFreeAsync(p, stream);
+        for (auto *p : d_tperm)
             if (p) cudaFreeAsync(p, stream);
         cudaStreamSynchronize(stream);
     }
@@ -316,7 +320,46 @@ int ensure_ws(relate_handle_s *h, int R) {
     return RELATE_OK;
 }
 
+void fill_stream_args(const relate_handle_s *h, int mode, MttkrpArgs &a) {
+    a.words = h->d_words;
+    a.vals = h->d_vals;
+    a.nnz = h->nnz;
+    a.S = h->S;
+    a.P = h->P;
+    a.N = h->N;
+    a.mode = mode;
+    a.fields = h->fields;
+    a.In = h->dims[mode];
+    a.plo = h->d_plo;
+    a.phi = h->d_phi;
+    a.hot_rows = h->d_hot_rows[mode];
+    a.maxcount = h->maxcount[mode];
+}
+
+// The tile order of a SEGMENTED mode (N <= 5): built once per handle and
+// mode, on `st`, unless `st` is being captured (then the kernel sorts).
+int ensure_tile_order(relate_handle_s *h, int mode, int R, cudaStream_t st) {
+    if (h->d_tperm[mode] || h->nnz == 0 || h->N > 5) return RELATE_OK;
+    if (resolve_conflict(h, mode, R) != RELATE_CONFLICT_SEGMENTED) return RELATE_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp: capture status");
+    if (cs != cudaStreamCaptureStatusNone) return RELATE_OK;
+    MttkrpArgs a{};
+    fill_stream_args(h, mode, a);
+    uint16_t *p = nullptr;
+    if ((e = dalloc(&p, tperm_bytes(h->nnz), st)) != cudaSuccess) return cuda_fail(e, "relate_mttkrp: tile order");
+    if ((e = launch_tile_order(a, h->KW, h->num_sms, p, st)) != cudaSuccess) {
+        cudaFreeAsync(p, st);
+        return cuda_fail(e, "relate_mttkrp: tile order");
+    }
+    h->d_tperm[mode] = p;
+    return RELATE_OK;
+}
+
 int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *out, cudaStream_t st) {
+    int rc0 = ensure_tile_order(h, mode, R, st);
+    if (rc0) return rc0;
     MttkrpArgs a{};
     a.words = h->d_words;
     a.vals = h->d_vals;
@@ -335,6 +378,7 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
     a.hot_rows = h->d_hot_rows[mode];
     a.maxcount = h->maxcount[mode];
     a.hot_scratch = h->d_hot_scratch;
+    a.tperm = h->d_tperm[mode];
     a.err = h->d_err;
     a.strategy = resolve_conflict(h, mode, R);
     const int accb = mttkrp_acc_bytes(h->factor_dtype);
@@ -723,6 +767,8 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     if (rc) return rc;
     const cudaStream_t st = h->stream;
     const int N = h->N;
+    for (int n = 0; n < N; n++)  // before any capture: tile orders are built once
+        if ((rc = ensure_tile_order(h, n, R, st)) != RELATE_OK) return rc;
     const int RR = R * R;
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_status, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "relate_cpals: setup");
@@ -876,7 +922,7 @@ int relate_footprint(const uint64_t *dims, int nmodes, int64_t nnz, const relate
     const int64_t S = p->partition_size > 0 ? p->partition_size : 4096;
     const int64_t P = (nnz + S - 1) / S;
     const size_t resident = words_bytes(nnz, kb) + vals_bytes(nnz, vb) + 2 * bounds_bytes(P, nmodes) + 64 + 16 +
-                            kHotScratchBytes +
+                            kHotScratchBytes + (size_t)nmodes * tperm_bytes(nnz) +
                             sumI * 4 + (size_t)nmodes * kHotMax * 4 + perm_bytes(nnz);
     size_t temps = 2 * (size_t)nnz * kb + 2 * (size_t)nnz * 4 + radix_sort_temp_bytes(nnz) + 64 + kSmallBytes +
                    2 * (size_t)kLutMaxBytes + hot_table_temp_bytes(maxI);

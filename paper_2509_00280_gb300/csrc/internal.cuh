@@ -159,6 +159,7 @@ struct MttkrpArgs {
     int hot_n;                 // hot rows cached in shared memory by this launch
     uint64_t maxcount;         // nonzeros of the mode's most populated row
     void *hot_scratch;         // SEGMENTED: per-block copies of the hot rows (kHotScratchBytes)
+    const uint16_t *tperm;     // SEGMENTED: precomputed tile order of the mode (null: sort in the kernel)
     int vals_f64;              // values stored as FP64 (else FP32)
     int *err;                  // device flag: bit 0 = a bounded wait timed out
     // record slot j of a decoded nonzero: slot 0 = the output mode, slots
@@ -183,6 +184,10 @@ cudaError_t launch_hot_table(const uint32_t *counts, uint64_t I, uint32_t *hot_r
 
 // Launches K5/K6/K7 for the given dtypes. factor_dtype / val_dtype are
 // relate_dtype_t. smem_budget: bytes available for shared accumulators.
+// Builds the tile order of a.mode into tperm (nnz 16-bit entries: position in
+// the tile sorted by output row | (1 + hot slot) << 11), for the SEGMENTED
+// MTTKRP kernel.
+cudaError_t launch_tile_order(const MttkrpArgs &a, int KW, int num_sms, uint16_t *tperm, cudaStream_t st);
 cudaError_t launch_mttkrp(const MttkrpArgs &a, int KW, int factor_dtype, int val_dtype,
                           int smem_budget, int num_sms, cudaStream_t st);
 

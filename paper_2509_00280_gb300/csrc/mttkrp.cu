@@ -94,8 +94,10 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
             if (a.strategy == RELATE_CONFLICT_ATOMIC)
                 hot = (16 * 1024) / (a.R * accb);
             else if (a.strategy == RELATE_CONFLICT_SEGMENTED && a.maxcount >= kSegHotMinCount && a.hot_scratch &&
-                     vec_ok && a.N >= 2 && a.N <= 5)
+                     a.tperm && vec_ok && a.N >= 2 && a.N <= 5) {  // the compile-time SEGMENTED kernel
                 hot = (int)(kHotBlockBytes / ((size_t)a.R * accb));
+                if (hot > mk::kTagMax) hot = mk::kTagMax;  // slots a tile-order entry can tag
+            }
         }
         if (hot > kHotMax) hot = kHotMax;
         if ((uint64_t)hot > a.In) hot = (int)a.In;
@@ -117,6 +119,29 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
     case RELATE_F32: return mttkrp_f32(a, KW, vec_ok, acc_bytes, (int)grid, st);
     default: return mttkrp_bf16(a, KW, vec_ok, acc_bytes, (int)grid, st);
     }
+}
+
+int tile_order_hot_rows(const MttkrpArgs &a) {
+    if (!a.hot_rows || a.In >= (1ull << 31) || a.maxcount < kSegHotMinCount) return 0;
+    uint64_t hot = mk::kTagMax;
+    if (hot > (uint64_t)kHotMax) hot = kHotMax;
+    if (hot > a.In) hot = a.In;
+    return (int)hot;
+}
+
+cudaError_t launch_tile_order(const MttkrpArgs &a_in, int KW, int num_sms, uint16_t *tperm, cudaStream_t st) {
+    MttkrpArgs a = a_in;
+    if (a.nnz == 0 || a.P == 0) return cudaSuccess;
+    a.hot_n = tile_order_hot_rows(a);
+    const int64_t tiles = a.P * ((a.S + mk::kTile - 1) / mk::kTile);
+    int64_t grid = (int64_t)num_sms * 4;
+    if (grid > tiles) grid = tiles;
+    switch (KW) {
+    case 1: mk::k_tile_order<1><<<(unsigned)grid, kThreads, 0, st>>>(a, tperm); break;
+    case 2: mk::k_tile_order<2><<<(unsigned)grid, kThreads, 0, st>>>(a, tperm); break;
+    default: mk::k_tile_order<4><<<(unsigned)grid, kThreads, 0, st>>>(a, tperm); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace relate

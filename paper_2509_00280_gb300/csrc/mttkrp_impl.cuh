@@ -180,6 +180,9 @@ template <typename C> struct GAdd<C, 1> {
 template <typename FT, int VPL> struct Unroll { static constexpr int U = 4; };
 
 constexpr int kTile = 2048;       // nonzeros per tile
+constexpr int kTileBits = 11;     // log2(kTile): a tile position in a tile-order entry
+static_assert((1 << kTileBits) == kTile, "tile positions take kTileBits bits");
+constexpr int kTagMax = (1 << (16 - kTileBits)) - 1;  // hot slots a 16-bit tile-order entry can tag
 constexpr int kItems = kTile / kThreads;
 constexpr int kSortBins = 2048;   // widest row range a tile may span to be sorted
 constexpr int kSortBinBits = 11;  // log2(kSortBins): hashed bins take this many bits
@@ -248,9 +251,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-// SEG = true: the SEGMENTED strategy fixed at compile time (sorted tiles, no
-// privatised output), so the flush and the record build carry no strategy
-// branches. Runs go to global memory. Runs of the mode's hottest rows (hot_n >
+// SEG = true: the SEGMENTED strategy fixed at compile time, with the mode's
+// precomputed tile order (a.tperm, k_tile_order) in place of the in-kernel
+// sort and no privatised output, so the flush and the record build carry no
+// strategy branches. Runs go to global memory. Runs of the mode's hottest rows (hot_n >
 // 0, tagged when the records are built) go to the block's own copy of those
 // rows in global scratch (a.hot_scratch, zeroed by the block, same vector
 // atomics), which the block adds into the output once at its end: a row
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
     for (int64_t i = threadIdx.x; i < acc_elems; i += kThreads) sacc[i] = C(0);
     if (SEG && hot_n)  // ordered before this block's atomics by the barriers that follow
         for (int i = threadIdx.x; i < hot_n * R; i += kThreads) hrep[i] = C(0);
-    if (hot_n) {  // hash set of this mode's hot rows (most populated first)
+    if (!SEG && hot_n) {  // hash set of this mode's hot rows (most populated first); SEG reads tags
         for (int i = threadIdx.x; i < kHotHash; i += kThreads) hkey[i] = 0xffffffffu;
         __syncthreads();
         for (int t = threadIdx.x; t < hot_n; t += kThreads) {
@@ -414,8 +418,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
         };
         // pass 1 counts rows; the warp-aggregated atomic returns the bin's
         // running count, so each nonzero learns its offset inside its bin
+        // SEG: the precomputed tile order replaces the sort; each nonzero
+        // reads its sorted position and hot tag from it in pass 2
         uint32_t ibin[kItems], ioff[kItems];
-        if (sorted) {
+        if (sorted && !SEG) {
             for (uint32_t i = threadIdx.x; i < nb; i += kThreads) bins[i] = 0;
             __syncthreads();
 #pragma unroll
@@ -476,7 +482,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
             if (j >= nt) continue;
             const Word w = sw[j];
             uint32_t p = (uint32_t)j, hbin = 0;
-            if (sorted) {
+            if (SEG) {
+                const uint32_t e = __ldg(a.tperm + b + j);
+                p = e & (kTile - 1);
+                hbin = e >> kTileBits;
+                if (hbin > (uint32_t)hot_n) hbin = 0;  // tagged for a larger hot set
+            } else if (sorted) {
                 const uint32_t bv = bins[ibin[i]];
                 p = (bv & 0xffffu) + ioff[i];
                 hbin = bv >> 16;
@@ -487,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
 #pragma unroll
             for (int k = 0; k < NI; k++) rec.idx[k] = k < N ? fld(w, a.rshift[k], a.rmask[k]) : 0u;
             if (hot_n) {  // slot 0 becomes the run's destination: 0x80000000|slot for a hot row
-                if (sorted && direct) {
+                if (SEG || (sorted && direct)) {
                     if (hbin) rec.idx[0] = 0x80000000u | (hbin - 1u);
                 } else {
                     const uint32_t hs = hot_slot_of(rec.idx[0]);
@@ -640,6 +651,116 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
     }
 }
 
+// Tile order of one mode, computed once per handle and mode: for every
+// nonzero, its position in its tile sorted by output row (the counting sort
+// of k_mttkrp: direct bins row - lo, or the hashed bins) in bits 0..10, and
+// 1 + the hot slot of its row (0 = not hot; slots < hot_n <= kTagMax) in
+// bits 11..15. One block per tile.
+template <int KW>
+__global__ void __launch_bounds__(kThreads) k_tile_order(const MttkrpArgs a, uint16_t *__restrict__ tperm) {
+    __shared__ uint32_t bins[kSortBins];
+    __shared__ uint32_t hkey[kHotHash], hval[kHotHash];
+    __shared__ uint32_t wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31;
+    const int N = a.N, mode = a.mode, hot_n = a.hot_n;
+    const int mshift = a.fields.shift[mode];
+    const uint32_t mmask = a.fields.mask[mode];
+    if (hot_n) {
+        for (int i = threadIdx.x; i < kHotHash; i += kThreads) hkey[i] = 0xffffffffu;
+        __syncthreads();
+        for (int t = threadIdx.x; t < hot_n; t += kThreads) {
+            const uint32_t row = __ldg(a.hot_rows + t);
+            if (row == 0xffffffffu) continue;
+            uint32_t h = hot_hash(row);
+            for (int probe = 0; probe < kHotHash; probe++, h = (h + 1) & (kHotHash - 1)) {
+                const uint32_t prev = atomicCAS(hkey + h, 0xffffffffu, row);
+                if (prev == 0xffffffffu) {
+                    hval[h] = (uint32_t)t;
+                    break;
+                }
+                if (prev == row) break;
+            }
+        }
+        __syncthreads();
+    }
+    auto hot_tag = [&](uint32_t row) -> uint32_t {  // 1 + slot, or 0
+        uint32_t h = hot_hash(row);
+        for (int probe = 0; probe < kHotHash; probe++, h = (h + 1) & (kHotHash - 1)) {
+            const uint32_t k = hkey[h];
+            if (k == row) return hval[h] + 1u;
+            if (k == 0xffffffffu) return 0u;
+        }
+        return 0u;
+    };
+    const int64_t tiles_per_part = (a.S + kTile - 1) / kTile;
+    const int64_t ntiles = a.P * tiles_per_part;
+    for (int64_t tq = blockIdx.x; tq < ntiles; tq += gridDim.x) {
+        const int64_t q = tq / tiles_per_part;
+        const int64_t b = q * a.S + (tq - q * tiles_per_part) * kTile;
+        const int64_t pe = min(q * a.S + a.S, a.nnz);
+        const int nt = (int)max((int64_t)0, min((int64_t)kTile, pe - b));
+        if (nt == 0) continue;
+        const uint32_t lo = a.plo[q * N + mode];
+        const uint32_t span = a.phi[q * N + mode] - lo + 1;
+        const bool direct = span <= (uint32_t)kSortBins;
+        const uint32_t nb = direct ? span : (uint32_t)kSortBins;
+        __syncthreads();  // the previous tile's bins are consumed
+        for (uint32_t i = threadIdx.x; i < nb; i += kThreads) bins[i] = 0;
+        __syncthreads();
+        uint32_t ibin[kItems], ioff[kItems], irow[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            const int j = i * kThreads + threadIdx.x;
+            const uint32_t row = j < nt ? fld(load_word<KW>(a.words, b + j), mshift, mmask) : 0u;
+            const uint32_t r = j < nt ? (direct ? row - lo : (row * 2654435761u) >> (32 - kSortBinBits)) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, r);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (r != 0xffffffffu && lane == leader) base = atomicAdd(bins + r, (uint32_t)__popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            ibin[i] = r;
+            ioff[i] = base + __popc(peers & lane_lt_mask());
+            irow[i] = row;
+        }
+        __syncthreads();
+        {   // exclusive scan of the bins, a contiguous slice per thread
+            constexpr int PER = kSortBins / kThreads;
+            const int base = threadIdx.x * PER;
+            uint32_t loc[PER];
+            uint32_t sum = 0;
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                loc[i] = base + i < (int)nb ? bins[base + i] : 0u;
+                sum += loc[i];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) wsum[threadIdx.x >> 5] = incl;
+            __syncthreads();
+            uint32_t run = incl - sum;
+            for (int w = 0; w < (threadIdx.x >> 5); w++) run += wsum[w];
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                if (base + i < (int)nb) bins[base + i] = run;
+                run += loc[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            const int j = i * kThreads + threadIdx.x;
+            if (j >= nt) continue;
+            const uint32_t p = bins[ibin[i]] + ioff[i];
+            const uint32_t tag = hot_n ? hot_tag(irow[i]) : 0u;
+            tperm[b + j] = (uint16_t)(p | (tag << kTileBits));
+        }
+    }
+}
+
 // Chooses lanes per group for R and launches one instantiation.
 template <int NT, int KW, typename FT, int VEC, int VPL, bool SEG = false>
 cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStream_t st) {
@@ -666,7 +787,7 @@ cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_byt
              : KW == 2 ? launch_one<NT_, 2, FT, V, 1, S_>(a, acc_bytes, grid, st)                \
                        : launch_one<NT_, 4, FT, V, 1, S_>(a, acc_bytes, grid, st))
 #define RELATE_MK_KW(NT_) (seg ? RELATE_MK_KW_S(NT_, true) : RELATE_MK_KW_S(NT_, false))
-    const bool seg = a.strategy == RELATE_CONFLICT_SEGMENTED;
+    const bool seg = a.strategy == RELATE_CONFLICT_SEGMENTED && a.tperm != nullptr;
     if (!vec_ok) {
         return KW == 1 ? launch_one<0, 1, FT, 1, 2>(a, acc_bytes, grid, st)
                        : KW == 2 ? launch_one<0, 2, FT, 1, 2>(a, acc_bytes, grid, st)
@@ -704,6 +825,7 @@ inline size_t tile_bytes_for(int N, int KW, int factor_dtype, bool vec_ok, int v
 }  // namespace mk
 
 cudaError_t mttkrp_f64(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st);
+
 cudaError_t mttkrp_f32(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st);
 cudaError_t mttkrp_bf16(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st);
 
