@@ -312,7 +312,12 @@ int ensure_ws(relate_handle_s *h, int R) {
         (e = dalloc((void **)&h->d_fit, 64, st)) != cudaSuccess ||
         (e = dalloc((void **)&h->d_status, 64, st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals workspace");
-    if (!h->aux && ((e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+    // the normal equations (one block) run at the highest stream priority so
+    // that the block scheduler places them before the waiting MTTKRP blocks
+    int prio_lo = 0, prio_hi = 0;
+    if (!h->aux && (e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals: stream priorities");
+    if (!h->aux && ((e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
                     (e = cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
                     (e = cudaEventCreateWithFlags(&h->ev_v, cudaEventDisableTiming)) != cudaSuccess))
         return cuda_fail(e, "relate_cpals: auxiliary stream");
@@ -797,7 +802,8 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
             return rc;
         }
         if (e2 != cudaSuccess) return cuda_fail(e2, "relate_cpals: end capture");
-        e = cudaGraphInstantiate(&gexec, g, 0);
+        // keep the captured per-node priorities (the normal equations' stream)
+        e = cudaGraphInstantiate(&gexec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(e, "relate_cpals: graph instantiate");
     }

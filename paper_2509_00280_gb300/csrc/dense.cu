@@ -288,10 +288,14 @@ __global__ void __launch_bounds__(kThreads) k_finish_mode(const double *__restri
         }
     }
     __syncthreads();
+    if (threadIdx.x < R) {  // reciprocals once per column
+        const double l = lam[threadIdx.x];
+        lam[threadIdx.x] = l > 0.0 ? 1.0 / l : 0.0;
+    }
+    __syncthreads();
     for (int idx = threadIdx.x; idx < R * R; idx += kThreads) {
         const int r = idx / R, s = idx % R;
-        const double d = lam[r] * lam[s];
-        G[idx] = d > 0.0 ? G[idx] / d : 0.0;
+        G[idx] = G[idx] * lam[r] * lam[s];
     }
 }
 
@@ -352,15 +356,19 @@ template <> __device__ __forceinline__ __nv_bfloat16 store_as<float, __nv_bfloat
 template <typename C, typename FT>
 __global__ void __launch_bounds__(kThreads) k_scale_store(const C *__restrict__ Mh, int64_t I, int R,
                                                           const double *__restrict__ lambda, FT *__restrict__ A) {
-    __shared__ C lam[MAXR];
-    for (int r = threadIdx.x; r < R; r += kThreads) lam[r] = (C)lambda[r];
-    __syncthreads();
-    const int64_t tot = I * R;
-    for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * kThreads) {
-        const int r = (int)(idx % R);
-        const C l = lam[r];
-        const C v = Mh[idx];
-        A[idx] = store_as<C, FT>(l > C(0) ? v / l : v);
+    // thread t owns column t % R of rows t / R, t / R + rows_per_pass, ...:
+    // coalesced, and no division or remainder per element (1 / lambda_r is
+    // formed once per thread)
+    const int rows_per_pass = kThreads / R;  // R <= 64 <= kThreads
+    const int t = threadIdx.x;
+    if (t >= rows_per_pass * R) return;
+    const int r = t % R;
+    const double l = lambda[r];
+    const C inv = l > 0.0 ? (C)(1.0 / l) : C(1);
+    for (int64_t row = (int64_t)blockIdx.x * rows_per_pass + t / R; row < I;
+         row += (int64_t)gridDim.x * rows_per_pass) {
+        const int64_t idx = row * R + r;
+        A[idx] = store_as<C, FT>(Mh[idx] * inv);
     }
 }
 
@@ -481,7 +489,8 @@ cudaError_t launch_finish_mode(const double *Vsave, int R, double *lambda, doubl
 cudaError_t launch_scale_store(const void *Mh, int64_t I, int R, int acc_dtype, const double *lambda, void *A,
                                int factor_dtype, cudaStream_t st) {
     if (I == 0) return cudaSuccess;
-    int64_t g64 = (I * R + kThreads - 1) / kThreads;
+    const int64_t rows_per_block = kThreads / R;
+    int64_t g64 = (I + rows_per_block - 1) / rows_per_block;
     const int g = (int)(g64 > 152 * 16 ? 152 * 16 : g64);
     if (factor_dtype == RELATE_F64)
         k_scale_store<double, double><<<g, kThreads, 0, st>>>((const double *)Mh, I, R, lambda, (double *)A);

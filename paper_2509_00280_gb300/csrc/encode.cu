@@ -383,8 +383,14 @@ __global__ void __launch_bounds__(kThreads) k_partition_stats(const typename Wor
                                                               uint32_t *__restrict__ plo, uint32_t *__restrict__ phi,
                                                               unsigned long long *__restrict__ runs,
                                                               CountPtrs counts_tbl) {
-    // one block per partition
+    // one block per partition: [lo_n, hi_n] and runs of each mode, then each
+    // mode's histogram of the partition, in shared memory when the
+    // partition's rows of the mode span at most kStatBins (one global
+    // addition per distinct row), else with warp-aggregated global atomics
+    constexpr int kStatBins = 4096;
     __shared__ uint32_t s_lo[kMaxModes][RS_WARPS], s_hi[kMaxModes][RS_WARPS], s_rn[kMaxModes][RS_WARPS];
+    __shared__ uint32_t s_blo[kMaxModes], s_bhi[kMaxModes];
+    __shared__ uint32_t hist[kStatBins];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q = blockIdx.x;
     const int64_t b = q * S, e = min(b + S, n);
@@ -395,32 +401,17 @@ __global__ void __launch_bounds__(kThreads) k_partition_stats(const typename Wor
         hi[m] = 0;
         rn[m] = 0;
     }
-    uint32_t *counts[kMaxModes];
-#pragma unroll
-    for (int m = 0; m < kMaxModes; m++) counts[m] = m < N ? counts_tbl.p[m] : nullptr;
-    // iterate in whole-warp steps so __match_any_sync sees full warps
-    for (int64_t j0 = b; j0 < e; j0 += kThreads) {
-        int64_t j = j0 + threadIdx.x;
-        bool ok = j < e;
-        typename WordT<KW>::T w{}, wp{};
-        if (ok) {
-            w = words[j];
-            if (j > b) wp = words[j - 1];
-        }
+    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) {
+        const typename WordT<KW>::T w = words[j];
+        typename WordT<KW>::T wp{};
+        if (j > b) wp = words[j - 1];
 #pragma unroll
         for (int m = 0; m < kMaxModes; m++) {
             if (m < N) {
-                uint32_t c = field_of<KW>(w, f.shift[m], f.mask[m]);
-                if (ok) {
-                    lo[m] = min(lo[m], c);
-                    hi[m] = max(hi[m], c);
-                    if (j == b || c != field_of<KW>(wp, f.shift[m], f.mask[m])) rn[m]++;
-                }
-                // warp-aggregated histogram increments
-                uint32_t key = ok ? c : 0xffffffffu;
-                uint32_t peers = __match_any_sync(0xffffffffu, key);
-                if (ok && lane == 31 - __clz(peers) && (uint64_t)c < counts_tbl.len[m])
-                    atomicAdd(counts[m] + c, (uint32_t)__popc(peers));
+                const uint32_t c = field_of<KW>(w, f.shift[m], f.mask[m]);
+                lo[m] = min(lo[m], c);
+                hi[m] = max(hi[m], c);
+                if (j == b || c != field_of<KW>(wp, f.shift[m], f.mask[m])) rn[m]++;
             }
         }
     }
@@ -449,9 +440,39 @@ __global__ void __launch_bounds__(kThreads) k_partition_stats(const typename Wor
             z = max(z, s_hi[m][w2]);
             r += s_rn[m][w2];
         }
+        s_blo[m] = a;
+        s_bhi[m] = z;
         plo[q * N + m] = a;
         phi[q * N + m] = z;
         atomicAdd(runs + m, (unsigned long long)r);
+    }
+    __syncthreads();
+    for (int m = 0; m < N; m++) {
+        const uint32_t mlo = s_blo[m], span = s_bhi[m] - mlo + 1;  // uniform
+        uint32_t *cm = counts_tbl.p[m];
+        const uint64_t len = counts_tbl.len[m];
+        if (span <= (uint32_t)kStatBins) {
+            for (uint32_t i = threadIdx.x; i < span; i += kThreads) hist[i] = 0;
+            __syncthreads();
+            for (int64_t j = b + threadIdx.x; j < e; j += kThreads) {
+                const uint32_t c = field_of<KW>(words[j], f.shift[m], f.mask[m]);
+                atomicAdd(hist + (c - mlo), 1u);
+            }
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < span; i += kThreads)
+                if (hist[i] && (uint64_t)mlo + i < len) atomicAdd(cm + mlo + i, hist[i]);
+            __syncthreads();  // hist is reused by the next mode
+        } else {
+            // whole-warp steps so that __match_any_sync sees full warps
+            for (int64_t j0 = b; j0 < e; j0 += kThreads) {
+                const int64_t j = j0 + threadIdx.x;
+                const bool ok = j < e;
+                const uint32_t c = ok ? field_of<KW>(words[j], f.shift[m], f.mask[m]) : 0xffffffffu;
+                // lanes past the end may share c's value: keep only valid peers
+                const uint32_t peers = __match_any_sync(0xffffffffu, c) & __ballot_sync(0xffffffffu, ok);
+                if (ok && lane == 31 - __clz(peers) && (uint64_t)c < len) atomicAdd(cm + c, (uint32_t)__popc(peers));
+            }
+        }
     }
 }
 
