@@ -423,8 +423,9 @@ int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_f
             return cuda_fail(e, "relate_cpals: normal equations");
         int rc = run_mttkrp(h, n, factors, R, h->d_M, st);
         if (rc) return rc;
-        if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess ||
-            (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess)
+        if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: mode update");
+        if (tc_path && (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess)
             return cuda_fail(e, "relate_cpals: mode update");
         if (tc_path) {
             // lambda from Ahat's column norms, store the normalised BF16
@@ -438,10 +439,10 @@ int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_f
                     cudaSuccess)
                 return cuda_fail(e, "relate_cpals: mode update");
         } else {
-            // solve, Gram and finish have consumed V^{-1} and V: the next
-            // mode's normal equations may overwrite them from here on
-            if ((e = launch_gram(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, st)) !=
-                    cudaSuccess ||
+            // the row pass with its Gram, then finish, have consumed V^{-1}
+            // and V: the next mode's normal equations may overwrite them
+            if ((e = launch_solve_gram(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_scratch,
+                                       h->d_G + n * RR, st)) != cudaSuccess ||
                 (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess)
                 return cuda_fail(e, "relate_cpals: mode update");
             if (n + 1 < N && (e = fork_normal_eq(n + 1)) != cudaSuccess)

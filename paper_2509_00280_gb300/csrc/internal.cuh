@@ -217,6 +217,10 @@ cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *V
                              double *Vsave, int f64_apply, int *status, cudaStream_t st);
 
 // In place, M (I x R, acc dtype) <- M V^{-1}.
+// launch_solve_rows followed by the Gram of the result into G (R x R FP64),
+// in one pass over the rows (the FP32/FP64 factor path).
+cudaError_t launch_solve_gram(void *M, int64_t I, int R, int acc_dtype, const double *Vinv, const float *Vinv32,
+                              double *scratch, double *G, cudaStream_t st);
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv,
                               const float *Vinv32, cudaStream_t st);
 
