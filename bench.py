@@ -39,10 +39,11 @@ CPU_SAMPLE_NNZ = 5_000_000  # nonzeros of the workload the CPU oracle runs per s
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": "adafd1b5e836d5d144442838d6a20caf80766c98907fe88038e79a787ec821f3",
-               # 20M-nonzero capture (296.3 MB per launch), stream part scaled
-               # to 50M nonzeros: 296.3 MB + 30M x 12 B
-               "bytes_per_launch": 656.3e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
+NCU_TRAFFIC = {"sha256": "5fc212c04dd25166b00a932a0e04ef8699e9cf31cf4e9b1693fa0ca16a66d829",
+               # 20M-nonzero capture (336.8 MB per launch), stream part (8-byte
+               # word, 4-byte value, 2-byte tile-order entry) scaled to 50M
+               # nonzeros: 336.8 MB + 30M x 14 B
+               "bytes_per_launch": 756.8e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
 
 
 def _peaks():

@@ -268,7 +268,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
     using R_t = Rec<NT, C>;
     constexpr int RB = RecStride<NT, C>::B;
     static_assert(sizeof(R_t) == RB, "records are indexed as an array of R_t");
-    constexpr int U = Unroll<FT, VPL>::U;
+    // nonzeros in flight per group: one more for the FP32/BF16 SEGMENTED
+    // kernel of 2-3 modes, whose records and row registers leave room for it
+    constexpr int U = (SEG && NT >= 2 && NT <= 3 && sizeof(C) == 4) ? Unroll<FT, VPL>::U + 1 : Unroll<FT, VPL>::U;
     constexpr int NI = R_t::NI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
