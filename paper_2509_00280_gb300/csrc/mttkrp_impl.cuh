@@ -7,18 +7,22 @@
 // reduction or atomics per mode from fiber reuse).
 //
 // GB300 mapping:
-//  * A block walks equal-work partitions of the sorted stream (grid-stride,
-//    so neighbouring blocks work on neighbouring partitions and share factor
-//    rows in L2).
-//  * Inside a block, a "group" of G lanes owns one nonzero at a time; each
-//    lane holds 16 bytes of the R-wide row (VEC elements), so a factor-row
-//    gather is G coalesced 16-byte loads (one 128-byte line for R = 32 FP32).
-//  * Each group walks a contiguous slice of the partition. Consecutive
-//    nonzeros with the same output row (runs of equal i_n in encoded order)
-//    are summed in registers; a run is flushed once:
-//      ATOMIC      -> global vector atomics (red.global.add.v4.f32 / f64),
-//      SEGMENTED   -> shared-memory atomics into a window over the
-//                     partition's [lo_n, hi_n] rows, flushed per partition,
+//  * A block walks 2048-nonzero tiles of the sorted stream (grid-stride, so
+//    neighbouring blocks work on neighbouring partitions and share factor
+//    rows in L2); a tile's words and values arrive by a TMA bulk copy.
+//  * The tile is ordered by output row in shared memory (a counting sort,
+//    or the mode's precomputed tile order) and each nonzero is decoded once
+//    into a record {value, i_n, i_k (k != n)}.
+//  * A "group" of G lanes owns one nonzero at a time; each lane holds 16
+//    bytes of the R-wide row (VEC elements), so a factor-row gather is G
+//    coalesced 16-byte loads (one 128-byte line for R = 32 FP32).
+//  * Each group walks a contiguous slice of the records. Consecutive
+//    nonzeros with the same output row are summed in registers; a run is
+//    flushed once:
+//      ATOMIC      -> global vector atomics (red.global.add.v4.f32 / f64), the
+//                     mode's hottest rows into shared-memory accumulators,
+//      SEGMENTED   -> global vector atomics after the sort (the hottest rows of
+//                     a skewed mode into the block's copy in global scratch),
 //      PRIVATIZED  -> shared-memory atomics into a block-private copy of the
 //                     whole output, flushed once per block.
 #pragma once
