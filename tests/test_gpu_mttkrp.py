@@ -191,3 +191,65 @@ def test_gram_bf16_tensor_cores_exact_on_integers(I, R):
     rl.relate_gram(t, R, "bf16", G)
     torch.cuda.synchronize()
     assert np.array_equal(G.cpu().numpy(), A.T @ A)
+
+
+@pytest.fixture(scope="module")
+def skewed():
+    """A tensor whose mode 0 has a row with ~40% of the nonzeros (so the
+    SEGMENTED kernel keeps per-block copies of its hot rows), and oracle
+    results per factor precision."""
+    spec = synth.TensorSpec("skewed3d", (50_000, 3000, 800), 400_000,
+                            (("zipf", 1.6), ("zipf", 1.1), ("zipf", 1.1)), seed=31)
+    c, v = synth.make_tensor(spec)
+    R = 32
+    fs = synth.init_factors(spec.dims, R, seed=3, dtype=np.float32)
+    refs = {}
+    for fdt in ("f64", "f32", "bf16"):
+        fr = [oracle.round_bf16(f).astype(np.float64) for f in fs] if fdt == "bf16" else \
+             [f.astype(np.float64) for f in fs]
+        refs[fdt] = [oracle.mttkrp(c, v.astype(np.float64), spec.dims, n, fr) for n in range(3)]
+    return spec, c, v, fs, R, refs
+
+
+@pytest.mark.parametrize("S", [2048, 3000, 1001, 8192])
+@pytest.mark.parametrize("fdt", ["f64", "f32", "bf16"])
+def test_segmented_tile_order_partition_sizes(skewed, S, fdt):
+    """The SEGMENTED kernel with its precomputed tile order and hot-row copies,
+    at partition sizes that give ragged tiles (3000, 8192), one tile per
+    partition (2048) and partitions that are not a multiple of 4 nonzeros
+    (1001: plain loads instead of TMA copies)."""
+    spec, c, v, fs, R, refs = skewed
+    vin = v.astype(np.float64) if fdt == "f64" else v
+    h = encode_dev(c, vin, spec.dims, factor_dtype=fdt, partition_size=S)
+    st = rl.relate_get_stats(h)
+    assert st["maxcount"][0] >= 1 << 15  # mode 0 takes the hot-row copies
+    for n in range(3):
+        rl.relate_set_conflict(h, n, rl.RELATE_CONFLICT_SEGMENTED)
+    dfs = factors_dev(fs, fdt)
+    tol = 1e-12 if fdt == "f64" else 1e-5
+    for n in range(3):
+        got = mttkrp_dev(h, n, dfs, R, acc="f64" if fdt == "f64" else "f32")
+        assert rel_fro(got, refs[fdt][n]) <= tol, (S, fdt, n)
+        again = mttkrp_dev(h, n, dfs, R, acc="f64" if fdt == "f64" else "f32")  # tile order reused
+        assert rel_fro(again, refs[fdt][n]) <= tol, (S, fdt, n)
+    h.close()
+
+
+@pytest.mark.parametrize("dims", [(20, 30, 40, 50, 60, 70), (5, 6, 7, 8, 9, 10, 11, 12)])
+def test_six_and_eight_modes(dims):
+    """N > 5 runs the generic instantiation (runtime N) of every strategy."""
+    rng = np.random.default_rng(len(dims))
+    nnz = 30_000
+    c = np.stack([rng.integers(0, d, nnz) for d in dims]).astype(np.uint32)
+    v = rng.random(nnz)
+    R = 16
+    fs = [rng.random((d, R)) for d in dims]
+    refs = [oracle.mttkrp(c, v, dims, n, fs) for n in range(len(dims))]
+    h = encode_dev(c, v, dims, factor_dtype="f64")
+    dfs = factors_dev(fs, "f64")
+    for strat in ("auto", "atomic", "segmented", "privatized"):
+        for n in range(len(dims)):
+            if strat != "auto":
+                rl.relate_set_conflict(h, n, STRATS[strat])
+            assert rel_fro(mttkrp_dev(h, n, dfs, R, acc="f64"), refs[n]) <= 1e-12, (strat, n)
+    h.close()

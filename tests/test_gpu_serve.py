@@ -91,3 +91,14 @@ def test_admission_respects_a_small_budget():
     # the pool's footprint estimate is an upper bound of what the request used
     free0, _ = torch.cuda.mem_get_info()
     assert max(fps) < free0
+
+
+def test_release_cached_memory_after_the_mix():
+    reqs = _mix(4, iters=2)
+    res, summ, _ = serve.run_mix(reqs, workers=2)
+    assert summ["requests"] == 4
+    torch.cuda.synchronize()
+    rl.relate_release_cached_memory()  # trims the pool; live handles: none
+    res2, _, _ = serve.run_mix(reqs, workers=2)  # the pool grows again on demand
+    for a, b in zip(res, res2):
+        assert a.iters == b.iters and abs(a.fit - b.fit) <= 1e-4
