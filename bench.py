@@ -168,11 +168,23 @@ def _algorithmic_bytes(stats, mode, R, fb, ab, vb):
     return b
 
 
-def _launches_per_step(stats, iters):
+def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
+    """Kernel launches of one step, counted from the library's launch
+    sequence (and checked against an ncu launch list):
+    encode = key build, 5 kernels per radix pass of the keys (ceil(l(p)/8)
+    passes) and of each mode's hot-row count sort (4 passes), word packing,
+    gather, partition statistics, per mode a histogram summary, a count and
+    a hot-row list, and the 2-kernel norm;
+    CP-ALS = the initial Grams (partial + reduce per mode), one tile order per
+    SEGMENTED mode, and per iteration per mode: normal equations, MTTKRP,
+    then row pass + Gram (fused) + reduce + finish + store (FP32/FP64) or row
+    pass + 2 column-norm kernels + store + tensor-core Gram + reduce +
+    inner products (BF16), plus the fit."""
     N = stats["nmodes"]
     passes = (stats["lp"] + 7) // 8
-    encode = 1 + 5 * passes + 1 + 1 + 1 + N + 2
-    cpals = 2 * N + iters * (7 * N + 1)
+    encode = 1 + 5 * (passes + 4 * N) + 1 + 1 + 1 + 3 * N + 2
+    per_mode = 9 if (fdt == "bf16" and R % 8 == 0) else 6
+    cpals = 2 * N + n_tile_orders + iters * (per_mode * N + 1)
     return encode + cpals
 
 
@@ -378,7 +390,8 @@ def main():
                              % (spec.nnz * (stats['key_bytes'] + vb) // 2 ** 20),
                        "final_fit": res["fit"]},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": _launches_per_step(stats, iters) * args.steps,
+            "gpu_launches": _launches_per_step(stats, iters, fdt, sum(1 for m in per_mode if m["strategy"] == 2),
+                                               R) * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_mttkrp", "per_mode": per_mode},
