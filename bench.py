@@ -179,12 +179,13 @@ def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
     SEGMENTED mode, and per iteration per mode: normal equations, MTTKRP,
     then row pass + Gram (fused) + reduce + finish + store (FP32/FP64) or row
     pass + 2 column-norm kernels + store + tensor-core Gram + reduce +
-    inner products (BF16), plus the fit."""
+    inner products (BF16), plus the fit and the kernel that records it."""
     N = stats["nmodes"]
     passes = (stats["lp"] + 7) // 8
     encode = 1 + 5 * (passes + 4 * N) + 1 + 1 + 1 + 3 * N + 2
     per_mode = 9 if (fdt == "bf16" and R % 8 == 0) else 6
-    cpals = 2 * N + n_tile_orders + iters * (per_mode * N + 1)
+    # graph replay with a fixed iteration count records each fit (1 kernel)
+    cpals = 2 * N + n_tile_orders + iters * (per_mode * N + 1 + 1)
     return encode + cpals
 
 

@@ -234,8 +234,13 @@ int relate_release_cached_memory(void);
  * call and replays it each iteration, instead of issuing the ~8N launches of
  * an iteration one by one. Results are those of the plain path (same kernels
  * in the same order). Needs a non-default stream (relate_set_stream); on the
- * legacy default stream the plain path runs. Default: disabled. The paper
- * has no counterpart (launch overhead only). Errors: INVALID_ARG. */
+ * legacy default stream the plain path runs. With tol <= 0 (a fixed number
+ * of iterations) the iterations are replayed back to back and relate_cpals
+ * synchronises once, at the end (each replay records its fit on the device);
+ * if an iteration's normal equations are not positive definite, the later
+ * iterations still run (on zeroed normal equations) and info reports the
+ * failing iteration and its fit. Default: disabled. The paper has no
+ * counterpart (launch overhead only). Errors: INVALID_ARG. */
 int relate_set_cpals_graph(relate_handle_t h, int enable);
 
 /* Copies the encoded stream out, in encoded (sorted) order, to DEVICE

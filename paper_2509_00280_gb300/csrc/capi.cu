@@ -396,7 +396,8 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
 
 // One ALS sweep over all modes plus the fit, enqueued on the handle's stream
 // (capturable): results land in the pinned host words fit / status.
-int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_fit, int *p_stat) {
+int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_fit, int *p_stat,
+                    double *d_trace = nullptr, int *d_counter = nullptr) {
     const cudaStream_t st = h->stream;
     const int N = h->N;
     const int RR = R * R;
@@ -453,6 +454,7 @@ int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_f
         }
     }
     if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess ||
+        (d_trace && (e = launch_record_fit(h->d_fit, h->d_status, d_trace, d_counter, st)) != cudaSuccess) ||
         (e = cudaMemcpyAsync(p_fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(p_stat, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(p_stat + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -792,23 +794,92 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     cudaGraphExec_t gexec = nullptr;
     // the legacy default stream cannot be captured: graph mode needs a stream
     const bool graph = h->use_graph && st != nullptr && iters > 0;
+    // graph mode with a fixed iteration count (tol <= 0): the iterations are
+    // replayed back to back and the host synchronises once, at the end; each
+    // replay records its fit on the device
+    const bool no_sync = graph && !(tol > 0.0);
+    double *d_trace = nullptr;
+    int *d_counter = nullptr;
+    if (no_sync) {
+        if ((e = dalloc(&d_trace, sizeof(double) * (size_t)iters + 16, st)) != cudaSuccess ||
+            (e = dalloc(&d_counter, 16, st)) != cudaSuccess || (e = cudaMemsetAsync(d_counter, 0, 16, st)) != cudaSuccess) {
+            if (d_trace) cudaFreeAsync(d_trace, st);
+            return cuda_fail(e, "relate_cpals: fit trace");
+        }
+    }
+    auto free_trace = [&]() {
+        if (d_trace) cudaFreeAsync(d_trace, st);
+        if (d_counter) cudaFreeAsync(d_counter, st);
+        d_trace = nullptr;
+        d_counter = nullptr;
+    };
     if (graph) {
         cudaGraph_t g = nullptr;
-        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            free_trace();
             return cuda_fail(e, "relate_cpals: begin capture");
-        rc = cpals_iteration(h, R, factors, p_fit, p_stat);
+        }
+        rc = cpals_iteration(h, R, factors, p_fit, p_stat, d_trace, d_counter);
         cudaError_t e2 = cudaStreamEndCapture(st, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);
+            free_trace();
             return rc;
         }
-        if (e2 != cudaSuccess) return cuda_fail(e2, "relate_cpals: end capture");
+        if (e2 != cudaSuccess) {
+            free_trace();
+            return cuda_fail(e2, "relate_cpals: end capture");
+        }
         // keep the captured per-node priorities (the normal equations' stream)
         e = cudaGraphInstantiate(&gexec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "relate_cpals: graph instantiate");
+        if (e != cudaSuccess) {
+            free_trace();
+            return cuda_fail(e, "relate_cpals: graph instantiate");
+        }
     }
-    for (int it = 1; it <= iters; it++) {
+    if (no_sync) {
+        for (int it = 1; it <= iters; it++)
+            if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) {
+                cudaGraphExecDestroy(gexec);
+                cudaStreamSynchronize(st);
+                free_trace();
+                return cuda_fail(e, "relate_cpals: graph launch");
+            }
+        std::vector<double> trace((size_t)iters);
+        int counter[4] = {0, 0, 0, 0};
+        if ((e = cudaMemcpyAsync(trace.data(), d_trace, sizeof(double) * iters, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(counter, d_counter, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            cudaGraphExecDestroy(gexec);
+            free_trace();
+            return cuda_fail(e, "relate_cpals: fit trace to host");
+        }
+        cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        free_trace();
+        // the last replay copied the status words to the pinned slots
+        hstatus[0] = p_stat[0];
+        hstatus[1] = p_stat[1];
+        hstatus[2] = p_stat[2];
+        // after a NOT_PD iteration the later ones ran on zeroed normal
+        // equations: report the fit and the count of the failing iteration
+        done = counter[1] > 0 ? counter[1] : iters;
+        fit = trace[(size_t)done - 1];
+        if (info && info->fit_trace)
+            for (int k = 0; k < done; k++) info->fit_trace[k] = trace[(size_t)k];
+        if (hstatus[2]) {
+            cudaMemsetAsync(h->d_err, 0, 16, st);
+            if (info) {
+                info->fit = fit;
+                info->iters = done;
+                info->status = RELATE_ERR_TIMEOUT;
+            }
+            return fail(RELATE_ERR_TIMEOUT, "relate_cpals: a bounded device wait timed out");
+        }
+    }
+    for (int it = 1; it <= iters && !no_sync; it++) {
         if (graph) {
             if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess) {
                 cudaGraphExecDestroy(gexec);

@@ -474,6 +474,19 @@ __global__ void __launch_bounds__(kThreads) k_fit(const double *__restrict__ G_a
     }
 }
 
+// Records the fit of a graph-replayed iteration: trace[counter[0]++] = fit;
+// counter[1] = the first iteration (1-based) whose normal equations were not
+// positive definite.
+__global__ void k_record_fit(const double *__restrict__ fit, const int *__restrict__ status,
+                             double *__restrict__ trace, int *__restrict__ counter) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int it = counter[0];
+        trace[it] = fit[0];
+        if (status[1] && counter[1] == 0) counter[1] = it + 1;
+        counter[0] = it + 1;
+    }
+}
+
 inline int rows_grid(int64_t I, int rows_per_block) {
     int64_t g = (I + rows_per_block - 1) / rows_per_block;
     if (g > GR_BLOCKS) g = GR_BLOCKS;
@@ -611,6 +624,11 @@ cudaError_t launch_scale_store(const void *Mh, int64_t I, int R, int acc_dtype, 
         k_scale_store<float, __nv_bfloat16><<<g, kThreads, 0, st>>>((const float *)Mh, I, R, lambda,
                                                                      (__nv_bfloat16 *)A);
     (void)acc_dtype;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record_fit(const double *fit, const int *status, double *trace, int *counter, cudaStream_t st) {
+    k_record_fit<<<1, 32, 0, st>>>(fit, status, trace, counter);
     return cudaGetLastError();
 }
 

@@ -240,6 +240,8 @@ cudaError_t launch_scale_store(const void *Mhat, int64_t I, int R, int acc_dtype
                                const double *lambda, void *A, int factor_dtype, cudaStream_t st);
 
 // fit after the last mode (device scalar out[0]).
+// trace[counter[0]++] = *fit; counter[1] = first NOT_PD iteration (1-based).
+cudaError_t launch_record_fit(const double *fit, const int *status, double *trace, int *counter, cudaStream_t st);
 cudaError_t launch_fit(const double *G_all, int N, int R, const double *lambda, const double *inner,
                        const double *normX2, double *fit, cudaStream_t st);
 

@@ -75,3 +75,43 @@ def test_tolerance_stop_and_warm_restart():
     r2 = rl.relate_cpals(h, 4, 2, 0.0, dfs)
     assert r2["fit"] >= r1["fit"] - 1e-9
     h.close()
+
+
+def _graph_run(c, v, dims, R, iters, tol, init, graph):
+    s = torch.cuda.Stream()
+    h = encode_dev(c, v, dims, factor_dtype="f64", stream=s)
+    rl.relate_set_cpals_graph(h, graph)
+    dfs = factors_dev(init, "f64")
+    torch.cuda.synchronize()
+    try:
+        res = rl.relate_cpals(h, R, iters, tol, dfs)
+    except rl.RelateError as e:
+        res = {"error": e.status}
+    h.close()
+    return res
+
+
+def test_graph_mode_with_tolerance_stops_like_the_plain_path():
+    spec = synth.scaled(synth.WORKLOADS["uniform3d-1000x1000x1000-1M"]["spec"], 50_000, dims=(100, 120, 90))
+    c, v = synth.make_tensor(spec)
+    init = synth.init_factors(spec.dims, 4, seed=0)
+    a = _graph_run(c, v, spec.dims, 4, 200, 1e-4, init, False)
+    b = _graph_run(c, v, spec.dims, 4, 200, 1e-4, init, True)
+    assert a["iters"] == b["iters"] < 200
+    assert np.max(np.abs(a["fit_trace"] - b["fit_trace"])) <= 1e-9
+
+
+def test_not_positive_definite_reported_in_both_graph_paths():
+    """A zero factor makes every V of the other modes zero (even after the
+    ridge retry): NOT_PD in the first iteration, with the per-iteration path,
+    and with the fixed-count replay that synchronises only at the end."""
+    rng = np.random.default_rng(4)
+    dims = (40, 30, 20)
+    c = np.stack([rng.integers(0, d, 3000) for d in dims]).astype(np.uint32)
+    v = rng.random(3000)
+    init = [rng.random((d, 4)) for d in dims]
+    init[1][:] = 0.0
+    for graph in (False, True):
+        for tol in (0.0, 1e-6):
+            res = _graph_run(c, v, dims, 4, 5, tol, init, graph)
+            assert res.get("error") == -6, (graph, tol, res)  # RELATE_ERR_NOT_PD
