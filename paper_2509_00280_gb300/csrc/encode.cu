@@ -21,21 +21,13 @@ namespace {
 
 using u128 = unsigned __int128;
 
-template <int KW> __device__ __forceinline__ typename WordT<KW>::T to_word(u128 p);
-template <> __device__ __forceinline__ uint32_t to_word<1>(u128 p) { return (uint32_t)p; }
-template <> __device__ __forceinline__ unsigned long long to_word<2>(u128 p) {
-    return (unsigned long long)p;
-}
-template <> __device__ __forceinline__ W128 to_word<4>(u128 p) {
+__device__ __forceinline__ W128 to_w128(u128 p) {
     W128 w;
     w.lo = (uint64_t)p;
     w.hi = (uint64_t)(p >> 64);
     return w;
 }
-
-__device__ __forceinline__ u128 from_word(uint32_t w) { return (u128)w; }
-__device__ __forceinline__ u128 from_word(unsigned long long w) { return (u128)w; }
-__device__ __forceinline__ u128 from_word(W128 w) { return ((u128)w.hi << 64) | (u128)w.lo; }
+__device__ __forceinline__ u128 from_w128(W128 w) { return ((u128)w.hi << 64) | (u128)w.lo; }
 
 __device__ __forceinline__ uint32_t digit_of(uint32_t k, int shift) { return (k >> shift) & 0xffu; }
 __device__ __forceinline__ uint32_t digit_of(unsigned long long k, int shift) {
@@ -43,10 +35,6 @@ __device__ __forceinline__ uint32_t digit_of(unsigned long long k, int shift) {
 }
 __device__ __forceinline__ uint32_t digit_of(W128 k, int shift) {
     return shift < 64 ? (uint32_t)(k.lo >> shift) & 0xffu : (uint32_t)(k.hi >> (shift - 64)) & 0xffu;
-}
-
-__device__ __forceinline__ u128 low_mask(int len) {
-    return len >= 128 ? ~(u128)0 : (((u128)1 << len) - 1);
 }
 
 // Integer type wide enough for a position of KW 32-bit limbs: 64-bit
@@ -60,58 +48,11 @@ template <typename P> __device__ __forceinline__ P low_bits(int len) {
 template <int KW> __device__ __forceinline__ typename WordT<KW>::T to_word_p(typename Pos<KW>::T p);
 template <> __device__ __forceinline__ uint32_t to_word_p<1>(unsigned long long p) { return (uint32_t)p; }
 template <> __device__ __forceinline__ unsigned long long to_word_p<2>(unsigned long long p) { return p; }
-template <> __device__ __forceinline__ W128 to_word_p<4>(u128 p) { return to_word<4>(p); }
+template <> __device__ __forceinline__ W128 to_word_p<4>(u128 p) { return to_w128(p); }
 template <int KW> __device__ __forceinline__ typename Pos<KW>::T from_word_p(typename WordT<KW>::T w);
 template <> __device__ __forceinline__ unsigned long long from_word_p<1>(uint32_t w) { return w; }
 template <> __device__ __forceinline__ unsigned long long from_word_p<2>(unsigned long long w) { return w; }
-template <> __device__ __forceinline__ u128 from_word_p<4>(W128 w) { return from_word(w); }
-
-// ------------------------------------------------------------------ K1
-template <int KW>
-__global__ void __launch_bounds__(kThreads) k_build_keys(const uint32_t *__restrict__ coords,
-                                                         const uint64_t *__restrict__ dims,
-                                                         int64_t n, int N, BitRuns runs,
-                                                         typename WordT<KW>::T *__restrict__ keys,
-                                                         uint32_t *__restrict__ idx,
-                                                         uint32_t *__restrict__ err) {
-    using P = typename Pos<KW>::T;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        P p = 0;
-        bool bad = false;
-        for (int m = 0; m < N; m++) {
-            uint32_t c = __ldg(coords + (int64_t)m * n + e);
-            bad |= (uint64_t)c >= dims[m];
-            for (int r = runs.mode_begin[m]; r < runs.mode_begin[m + 1]; r++) {
-                P bits = (P)((c >> runs.src[r]) & (uint32_t)(((uint64_t)1 << runs.len[r]) - 1));
-                p |= bits << runs.dst[r];
-            }
-        }
-        if (bad) atomicOr(err, 1u);
-        keys[e] = to_word_p<KW>(p);
-        idx[e] = (uint32_t)e;
-    }
-}
-
-// p -> stored word: bits [dst, dst+len) of p go to field_off[m] + src.
-template <int KW>
-__global__ void __launch_bounds__(kThreads) k_make_words(const typename WordT<KW>::T *__restrict__ keys,
-                                                         int64_t n, BitRuns runs,
-                                                         typename WordT<KW>::T *__restrict__ words) {
-    using P = typename Pos<KW>::T;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const P p = from_word_p<KW>(keys[e]);
-        P w = 0;
-        for (int m = 0; m < kMaxModes; m++) {
-            for (int r = runs.mode_begin[m]; r < runs.mode_begin[m + 1]; r++) {
-                const P bits = (p >> runs.dst[r]) & low_bits<P>(runs.len[r]);
-                w |= bits << (runs.field_off[m] + runs.src[r]);
-            }
-        }
-        words[e] = to_word_p<KW>(w);
-    }
-}
+template <> __device__ __forceinline__ u128 from_word_p<4>(W128 w) { return from_w128(w); }
 
 template <int KW>
 __global__ void __launch_bounds__(kThreads) k_words_to_keys(const typename WordT<KW>::T *__restrict__ words,
@@ -632,19 +573,6 @@ size_t radix_sort_temp_bytes(int64_t n) {
     return sizeof(uint32_t) * (size_t)(hlen + nchunks + 16);
 }
 
-cudaError_t launch_build_keys(int KW, const uint32_t *coords, const uint64_t *dims_dev, int64_t n, int N,
-                              const BitRuns &runs, void *keys, uint32_t *idx, uint32_t *err,
-                              cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    const int g = grid_for(n);
-    switch (KW) {
-    case 1: k_build_keys<1><<<g, kThreads, 0, st>>>(coords, dims_dev, n, N, runs, (uint32_t *)keys, idx, err); break;
-    case 2: k_build_keys<2><<<g, kThreads, 0, st>>>(coords, dims_dev, n, N, runs, (unsigned long long *)keys, idx, err); break;
-    default: k_build_keys<4><<<g, kThreads, 0, st>>>(coords, dims_dev, n, N, runs, (W128 *)keys, idx, err); break;
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t radix_sort_pairs(int KW, void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt, int64_t n,
                              int lp, void *temp, size_t temp_bytes, cudaStream_t st, bool *in_alt) {
     if (temp_bytes < radix_sort_temp_bytes(n)) return cudaErrorInvalidValue;
@@ -653,18 +581,6 @@ cudaError_t radix_sort_pairs(int KW, void *keys, uint32_t *vals, void *keys_alt,
     case 2: return rs_passes<unsigned long long>((unsigned long long *)keys, vals, (unsigned long long *)keys_alt, vals_alt, n, lp, temp, st, in_alt);
     default: return rs_passes<W128>((W128 *)keys, vals, (W128 *)keys_alt, vals_alt, n, lp, temp, st, in_alt);
     }
-}
-
-cudaError_t launch_make_words(int KW, const void *keys, int64_t n, const BitRuns &runs, void *words,
-                              cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    const int g = grid_for(n);
-    switch (KW) {
-    case 1: k_make_words<1><<<g, kThreads, 0, st>>>((const uint32_t *)keys, n, runs, (uint32_t *)words); break;
-    case 2: k_make_words<2><<<g, kThreads, 0, st>>>((const unsigned long long *)keys, n, runs, (unsigned long long *)words); break;
-    default: k_make_words<4><<<g, kThreads, 0, st>>>((const W128 *)keys, n, runs, (W128 *)words); break;
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_words_to_keys(int KW, const void *words, int64_t n, const BitRuns &runs, uint64_t *out2,

@@ -92,16 +92,6 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void pair_index(int p, int R, int &r, int &s) {
-    int row = 0, left = p;
-    while (left >= R - row) {
-        left -= R - row;
-        row++;
-    }
-    r = row;
-    s = row + left;
-}
-
 // Per-block upper-triangle partials (FP64) of A^T A, A BF16 I x R (R <= 64,
 // R % 8 == 0 so a row is a whole number of 16-byte vectors).
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const __nv_bfloat16 *__restrict__ A, int64_t I, int R,

@@ -68,12 +68,6 @@ template <> struct WordT<4> { using T = W128; };
 // Temporary device memory the radix sort needs for n keys of KW limbs.
 size_t radix_sort_temp_bytes(int64_t n);
 
-// Builds p for every nonzero (K1) and the identity payload; sets *err to 1
-// if some coordinate is out of range.
-cudaError_t launch_build_keys(int KW, const uint32_t *coords, const uint64_t *dims_dev, int64_t n,
-                              int N, const BitRuns &runs, void *keys, uint32_t *idx,
-                              uint32_t *err, cudaStream_t st);
-
 // Stable LSD radix sort of (key, payload) over bits [0, lp) (K2). The
 // result ends in (keys, vals) or (keys_alt, vals_alt); *in_alt tells which.
 cudaError_t radix_sort_pairs(int KW, void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt,
@@ -101,10 +95,6 @@ cudaError_t launch_build_keys_lut(int KW, const uint32_t *coords, const uint64_t
                                   cudaStream_t st);
 cudaError_t launch_make_words_lut(int KW, const void *keys, int64_t n, const ByteLuts &d, const void *tables,
                                   void *words, cudaStream_t st);
-
-// p (sorted) -> stored word with concatenated coordinate fields.
-cudaError_t launch_make_words(int KW, const void *keys, int64_t n, const BitRuns &runs, void *words,
-                              cudaStream_t st);
 
 // stored word -> p (for export / tests).
 cudaError_t launch_words_to_keys(int KW, const void *words, int64_t n, const BitRuns &runs,

@@ -74,51 +74,6 @@ __device__ __forceinline__ uint32_t fld(W128 w, int s, uint32_t m) {
     return (uint32_t)x & m;
 }
 
-// 16-byte (or scalar) load of vector j of a factor row, converted to C.
-template <typename FT, int VEC> struct VecLoad;
-template <> struct VecLoad<double, 2> {
-    static __device__ __forceinline__ void run(const double *row, int j, double (&x)[2]) {
-        double2 v = __ldg(reinterpret_cast<const double2 *>(row) + j);
-        x[0] = v.x;
-        x[1] = v.y;
-    }
-};
-template <> struct VecLoad<float, 4> {
-    static __device__ __forceinline__ void run(const float *row, int j, float (&x)[4]) {
-        float4 v = __ldg(reinterpret_cast<const float4 *>(row) + j);
-        x[0] = v.x;
-        x[1] = v.y;
-        x[2] = v.z;
-        x[3] = v.w;
-    }
-};
-template <> struct VecLoad<__nv_bfloat16, 4> {
-    static __device__ __forceinline__ void run(const __nv_bfloat16 *row, int j, float (&x)[4]) {
-        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row) + j);
-        x[0] = __uint_as_float(u.x << 16);
-        x[1] = __uint_as_float(u.x & 0xffff0000u);
-        x[2] = __uint_as_float(u.y << 16);
-        x[3] = __uint_as_float(u.y & 0xffff0000u);
-    }
-};
-template <> struct VecLoad<__nv_bfloat16, 8> {
-    static __device__ __forceinline__ void run(const __nv_bfloat16 *row, int j, float (&x)[8]) {
-        uint4 u = __ldg(reinterpret_cast<const uint4 *>(row) + j);
-        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            x[2 * i] = __uint_as_float(w[i] << 16);             // low bf16
-            x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);  // high bf16
-        }
-    }
-};
-template <typename FT> struct VecLoad<FT, 1> {
-    using C = typename Prec<FT>::C;
-    static __device__ __forceinline__ void run(const FT *row, int j, C (&x)[1]) {
-        x[0] = (C)row[j];
-    }
-};
-
 // Load of VEC consecutive elements of a factor row at p (16-byte aligned for
 // the vector forms), converted to C.
 template <typename FT, int VEC> struct VecLoadP;
