@@ -283,6 +283,22 @@ struct AsyncBufs {
     }
 };
 
+// The handle's second stream and its two events. The normal equations (one
+// block) run on it at the highest stream priority, so that the block
+// scheduler places them before the waiting MTTKRP blocks; relate_encode
+// copies host values on it while the keys are built and sorted.
+cudaError_t ensure_aux(relate_handle_s *h) {
+    if (h->aux) return cudaSuccess;
+    int prio_lo = 0, prio_hi = 0;
+    cudaError_t e;
+    if ((e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_v, cudaEventDisableTiming)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
 int ensure_ws(relate_handle_s *h, int R) {
     if (h->ws_R >= R && h->d_M) return RELATE_OK;
     const cudaStream_t st = h->stream;
@@ -312,15 +328,7 @@ int ensure_ws(relate_handle_s *h, int R) {
         (e = dalloc((void **)&h->d_fit, 64, st)) != cudaSuccess ||
         (e = dalloc((void **)&h->d_status, 64, st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals workspace");
-    // the normal equations (one block) run at the highest stream priority so
-    // that the block scheduler places them before the waiting MTTKRP blocks
-    int prio_lo = 0, prio_hi = 0;
-    if (!h->aux && (e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi)) != cudaSuccess)
-        return cuda_fail(e, "relate_cpals: stream priorities");
-    if (!h->aux && ((e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
-                    (e = cudaEventCreateWithFlags(&h->ev_g, cudaEventDisableTiming)) != cudaSuccess ||
-                    (e = cudaEventCreateWithFlags(&h->ev_v, cudaEventDisableTiming)) != cudaSuccess))
-        return cuda_fail(e, "relate_cpals: auxiliary stream");
+    if ((e = ensure_aux(h)) != cudaSuccess) return cuda_fail(e, "relate_cpals: auxiliary stream");
     h->ws_R = R;
     return RELATE_OK;
 }
@@ -597,6 +605,20 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
     int rc = RELATE_OK;
     {
         AsyncBufs tmp{st, {}};
+        // joins the value copy into `st` before the temporaries are released,
+        // on every path (declared after `tmp`, so it is destroyed first)
+        struct ValsJoin {
+            relate_handle_s *h;
+            cudaStream_t st;
+            bool pending = false;
+            cudaError_t join() {
+                pending = false;
+                return cudaStreamWaitEvent(st, h->ev_v, 0);
+            }
+            ~ValsJoin() {
+                if (pending) cudaStreamWaitEvent(st, h->ev_v, 0);
+            }
+        } vals_join{h, st};
         void *d_coords = nullptr, *d_vin = nullptr, *keys = nullptr, *keys_alt = nullptr, *idx = nullptr,
              *idx_alt = nullptr, *sort_tmp = nullptr, *d_dims = nullptr, *d_small = nullptr;
         const size_t sort_bytes = radix_sort_temp_bytes(nnz);
@@ -635,8 +657,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
                 goto done;
             }
             if ((e = cudaMemcpyAsync(d_coords, coords, (size_t)N * nnz * 4, cudaMemcpyHostToDevice, st)) !=
-                    cudaSuccess ||
-                (e = cudaMemcpyAsync(d_vin, vals, (size_t)nnz * vb, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+                cudaSuccess) {
                 rc = cuda_fail(e, "relate_encode: host-to-device copy");
                 goto done;
             }
@@ -670,6 +691,23 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
             rc = cuda_fail(e, "relate_encode: permutation tables");
             goto done;
         }
+        if (d_vin) {
+            // the values are first needed by the gather after the sort: they
+            // cross on the second stream behind the coordinates and the
+            // tables (copies share the copy engine and the link), while the
+            // keys are built and sorted
+            if ((e = ensure_aux(h)) != cudaSuccess || (e = cudaEventRecord(h->ev_g, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: copy stream");
+                goto done;
+            }
+            if ((e = cudaMemcpyAsync(d_vin, vals, (size_t)nnz * vb, cudaMemcpyHostToDevice, h->aux)) == cudaSuccess)
+                vals_join.pending = true;
+            if (e != cudaSuccess || (e = cudaEventRecord(h->ev_v, h->aux)) != cudaSuccess) {
+                rc = cuda_fail(e, "relate_encode: host-to-device copy");
+                goto done;
+            }
+        }
         bool in_alt = false;
         if ((e = launch_build_keys_lut(h->KW, c_dev, (const uint64_t *)d_dims, nnz, N, key_luts, d_luts, keys,
                                        (uint32_t *)idx, d_err, st)) != cudaSuccess ||
@@ -684,6 +722,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
             (e = cudaMemcpyAsync(h->d_perm, sperm, nnz * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
             (e = launch_make_words_lut(h->KW, skeys, nnz, word_luts, (const unsigned char *)d_luts + kLutMaxBytes,
                                        h->d_words, st)) != cudaSuccess ||
+            (vals_join.pending && (e = vals_join.join()) != cudaSuccess) ||
             (e = launch_gather(v_dev, sperm, nnz, vb, h->d_vals, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: words / gather");
             goto done;
