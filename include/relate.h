@@ -58,10 +58,15 @@ typedef enum { RELATE_F64 = 0, RELATE_F32 = 1, RELATE_BF16 = 2 } relate_dtype_t;
  *               registers and added to the output with global vector atomics,
  *               except the mode's most populated rows (up to 256), which
  *               accumulate in shared memory and are flushed once per block.
- *  SEGMENTED  - every 2048-nonzero tile is first sorted by i_n in shared memory
- *               (bins = rows of the partition's [lo_n, hi_n] range, or a hash
- *               of the row when that range is wider than 2048), so each run of
- *               equal rows is merged in registers and written once per tile.
+ *  SEGMENTED  - every 2048-nonzero tile is processed in an order sorted by i_n
+ *               (a counting sort with bins = rows of the partition's
+ *               [lo_n, hi_n] range, or a hash of the row when that range is
+ *               wider than 2048; computed once per handle and mode on the
+ *               mode's first MTTKRP and kept, 2 bytes per nonzero), so each
+ *               run of equal rows is merged in registers and written once per
+ *               tile; in a mode whose hottest row has >= 2^15 nonzeros, runs
+ *               of its hottest rows go to per-block copies in handle-owned
+ *               scratch, added into the output once per block.
  *  PRIVATIZED - sorted tiles as SEGMENTED, and the whole output (I_n x R) is
  *               privatised in shared memory per thread block and flushed once
  *               per block (only when it fits; otherwise SEGMENTED runs).
@@ -139,10 +144,13 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
  * by this call). R in [1, 64]. Asynchronous on `stream`; never synchronises.
  * Factor rows are read with 16-byte vector loads when every factor pointer
  * is 16-byte aligned and R * sizeof(factor) is a multiple of 16; otherwise
- * a scalar path runs. Calls on one handle must be ordered (one stream, or
+ * a scalar path runs. The first call for a SEGMENTED mode also builds the
+ * mode's tile order (one stream-ordered allocation and one kernel on
+ * `stream`; skipped while `stream` is being captured, the kernel then sorts
+ * each tile itself). Calls on one handle must be ordered (one stream, or
  * events): the SEGMENTED strategy keeps per-block copies of a skewed mode's
- * hottest rows in scratch owned by the handle. Errors: INVALID_ARG, CUDA
- * (launch failure). */
+ * hottest rows in scratch owned by the handle. Errors: INVALID_ARG, OOM,
+ * CUDA (launch failure). */
 int relate_mttkrp(relate_handle_t h, int mode, void *const *factors, int R, void *out,
                   void *stream);
 
@@ -166,7 +174,9 @@ typedef struct {
  * factors: host array of nmodes DEVICE pointers (handle's factor dtype),
  * in = initial factors, out = normalised factors. lambda: HOST, R doubles,
  * out. info: nullable. Runs on the handle's stream; synchronises once per
- * iteration (the fit). Errors: INVALID_ARG, NOT_PD, OOM, TIMEOUT, CUDA. */
+ * iteration (the fit), or once per call in graph mode with tol <= 0
+ * (relate_set_cpals_graph). Errors: INVALID_ARG, NOT_PD, OOM, TIMEOUT,
+ * CUDA. */
 int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *factors,
                  double *lambda, relate_cpals_info_t *info);
 
@@ -231,7 +241,7 @@ int relate_release_cached_memory(void);
 /* enable != 0: relate_cpals captures one ALS iteration (every mode's MTTKRP,
  * normal equations, solve, Gram and normalisation, the fit, and the copy of
  * the fit and status words to pinned host memory) as a CUDA graph once per
- * call and replays it each iteration, instead of issuing the ~8N launches of
+ * call and replays it each iteration, instead of issuing the ~6N launches of
  * an iteration one by one. Results are those of the plain path (same kernels
  * in the same order). Needs a non-default stream (relate_set_stream); on the
  * legacy default stream the plain path runs. With tol <= 0 (a fixed number
@@ -283,7 +293,10 @@ int relate_gram_noalloc(const void *A, int64_t I, int R, relate_dtype_t dtype, d
  * iteration limit instead of spinning forever. Returns RELATE_OK otherwise. */
 int relate_sync_status(relate_handle_t h, void *stream);
 
-/* Frees the handle and all its device memory (synchronises its stream). */
+/* Frees the handle and all its device memory (synchronises its stream and
+ * its second stream, not the device). The memory returns to the library's
+ * pool (see relate_release_cached_memory). Work that uses the handle on
+ * other streams must be complete. */
 void relate_free(relate_handle_t h);
 
 /* Static description of a status code. */
