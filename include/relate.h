@@ -289,8 +289,13 @@ int relate_gram_noalloc(const void *A, int64_t I, int R, relate_dtype_t dtype, d
 
 /* Synchronises `stream` and reports whether any kernel of this handle gave
  * up a bounded device wait since the last call (RELATE_ERR_TIMEOUT; the flag
- * is then cleared). The MTTKRP kernel waits on its own tile copies with an
- * iteration limit instead of spinning forever. Returns RELATE_OK otherwise. */
+ * is then cleared). The MTTKRP kernel waits on its own tile copies with a
+ * limit of 4e9 SM clock cycles (about 2 s) instead of spinning forever, then
+ * sets the flag and returns. Returns RELATE_OK otherwise.
+ * Test hook (environment variable, read at each call): RELATE_FAULT=alloc
+ * makes every library allocation fail (RELATE_ERR_OOM); RELATE_FAULT=timeout
+ * makes every MTTKRP launch skip its first tile copy with a ~50 ms wait limit,
+ * so that its bounded wait runs out and this call reports the timeout. */
 int relate_sync_status(relate_handle_t h, void *stream);
 
 /* Frees the handle and all its device memory (synchronises its stream and

@@ -2,6 +2,7 @@
 // the device-memory lifetime of an encoding, the encode pipeline, MTTKRP
 // dispatch and the CP-ALS driver loop.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -67,9 +68,19 @@ cudaError_t lib_pool(cudaMemPool_t *out) {
     return cudaSuccess;
 }
 
+// Test hook: RELATE_FAULT=alloc makes every library allocation fail (as if
+// the device were out of memory); RELATE_FAULT=timeout makes every MTTKRP
+// launch skip its first tile copy with a 1e8-cycle wait limit, so that the
+// bounded wait runs out and the launch reports a timeout. Unset in normal use.
+bool fault_is(const char *what) {
+    const char *f = getenv("RELATE_FAULT");
+    return f && strcmp(f, what) == 0;
+}
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
+    if (fault_is("alloc")) return cudaErrorMemoryAllocation;
     cudaMemPool_t pool = nullptr;
     const cudaError_t e = lib_pool(&pool);
     if (e != cudaSuccess) return e;
@@ -392,6 +403,10 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
     a.maxcount = h->maxcount[mode];
     a.hot_scratch = h->d_hot_scratch;
     a.tperm = h->d_tperm[mode];
+    if (fault_is("timeout")) {
+        a.fault_skip_copy = 1;
+        a.wait_cycles = 100000000LL;  // ~50 ms
+    }
     a.err = h->d_err;
     a.strategy = resolve_conflict(h, mode, R);
     const int accb = mttkrp_acc_bytes(h->factor_dtype);

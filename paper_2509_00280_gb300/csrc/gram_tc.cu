@@ -60,11 +60,13 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait (~2^22 polls, well over a second); false when it gave up.
+// Bounded wait (kWaitCycles SM clock cycles); false when it gave up.
 __device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); it++)
-        if (mbar_try(bar, parity)) return true;
-    return false;
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {

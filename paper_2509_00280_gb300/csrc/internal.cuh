@@ -150,6 +150,8 @@ struct MttkrpArgs {
     uint64_t maxcount;         // nonzeros of the mode's most populated row
     void *hot_scratch;         // SEGMENTED: per-block copies of the hot rows (kHotScratchBytes)
     const uint16_t *tperm;     // SEGMENTED: precomputed tile order of the mode (null: sort in the kernel)
+    long long wait_cycles;     // limit of a bounded wait, SM clock cycles (0: kWaitCycles)
+    int fault_skip_copy;       // test hook: never issue the first tile copy (its wait times out)
     int vals_f64;              // values stored as FP64 (else FP32)
     int *err;                  // device flag: bit 0 = a bounded wait timed out
     // record slot j of a decoded nonzero: slot 0 = the output mode, slots
@@ -158,6 +160,9 @@ struct MttkrpArgs {
     uint32_t rmask[kMaxModes];
     const void *rfac[kMaxModes];
 };
+
+// Limit of a bounded device wait: 4e9 SM cycles, about 2 s at 2 GHz.
+constexpr long long kWaitCycles = 4000000000LL;
 
 // Upper bound of hot (most populated) rows per mode kept in shared memory.
 constexpr int kHotMax = 256;

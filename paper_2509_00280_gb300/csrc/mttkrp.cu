@@ -43,6 +43,7 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
                           int num_sms, cudaStream_t st) {
     MttkrpArgs a = a_in;
     if (a.nnz == 0 || a.P == 0) return cudaSuccess;
+    if (a.wait_cycles <= 0) a.wait_cycles = kWaitCycles;
     const int accb = mttkrp_acc_bytes(factor_dtype);
     const int fb = factor_dtype == RELATE_F64 ? 8 : factor_dtype == RELATE_F32 ? 4 : 2;
 

@@ -203,11 +203,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^22 polls (well over a second) and reports it.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < (1u << 22); it++)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+// Bounded wait: gives up after `limit` SM clock cycles and reports it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
 }
 
 // SEG = true: the SEGMENTED strategy fixed at compile time, with the mode's
@@ -333,7 +335,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncthreads();
-        if (threadIdx.x == 0 && blockIdx.x < ntiles) issue(blockIdx.x);
+        // fault_skip_copy (a test hook): the first tile's copy is never issued,
+        // so its bounded wait runs out and the launch reports a timeout
+        if (threadIdx.x == 0 && blockIdx.x < ntiles && !a.fault_skip_copy) issue(blockIdx.x);
     }
     uint32_t phase = 0;
 
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
         }
         const int64_t q = tq / tiles_per_part;
         if (use_tma) {
-            const bool ok = mbar_wait_bounded(bar, phase);
+            const bool ok = mbar_wait_bounded(bar, phase, a.wait_cycles);
             phase ^= 1;
             if (__syncthreads_or(!ok)) {  // a copy never landed: report and stop
                 if (threadIdx.x == 0) atomicOr(a.err, 1);
