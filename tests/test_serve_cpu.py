@@ -158,3 +158,16 @@ def test_footprint_is_host_only_and_consistent():
         rl.relate_footprint((2 ** 33, 4), 10, 8)
     with pytest.raises(rl.RelateError):
         rl.relate_footprint((10, 10), 10, 65)
+
+
+def test_with_precision_keeps_the_tensor_and_widens_fp64_values():
+    import numpy as np
+    from paper_2509_00280_gb300.serve import Request, with_precision
+    c = np.zeros((3, 5), dtype=np.uint32)
+    v = np.arange(5, dtype=np.float32)
+    reqs = [Request(c, v, (4, 4, 4), 8, rid=0)]
+    f64 = with_precision(reqs, "f64")[0]
+    assert f64.precision == "f64" and f64.vals.dtype == np.float64 and np.array_equal(f64.vals, v)
+    assert f64.coords is c and reqs[0].precision == "f32" and reqs[0].vals.dtype == np.float32
+    bf = with_precision(reqs, "bf16")[0]
+    assert bf.precision == "bf16" and bf.vals is v
