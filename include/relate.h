@@ -71,7 +71,10 @@ typedef enum { RELATE_F64 = 0, RELATE_F32 = 1, RELATE_BF16 = 2 } relate_dtype_t;
  *               privatised in shared memory per thread block and flushed once
  *               per block (only when it fits; otherwise SEGMENTED runs).
  *  AUTO       - chosen per mode from the encode-time statistics:
- *               PRIVATIZED if I_n x R x acc bytes <= 32 KB, else SEGMENTED if
+ *               PRIVATIZED if I_n x R x acc bytes <= 32 KB (but SEGMENTED when
+ *               the mode has <= 31 rows, I_n x R x acc bytes <= 8 KB, its
+ *               hottest row >= 2^15 nonzeros, N <= 5 and 16-byte rows: every
+ *               row then sits in the per-block copies), else SEGMENTED if
  *               nnz / distinct(i_n) >= 8 or the mean run of equal i_n >= 8,
  *               else ATOMIC. */
 typedef enum {

@@ -224,8 +224,17 @@ relate_conflict_t resolve_conflict(const relate_handle_s *h, int mode, int R) {
     if (h->conflict[mode] != RELATE_CONFLICT_AUTO) return h->conflict[mode];
     const int accb = mttkrp_acc_bytes(h->factor_dtype);
     const uint64_t priv_bytes = h->dims[mode] * (uint64_t)R * accb;
-    // whole-output privatisation when it leaves room for two blocks per SM
-    if (priv_bytes <= 32u * 1024u) return RELATE_CONFLICT_PRIVATIZED;
+    // whole-output privatisation when it leaves room for two blocks per SM;
+    // except a short, heavily populated mode on the vector path: the
+    // SEGMENTED kernel then keeps every one of its rows in its per-block
+    // copies, and runs 1.3x faster than privatising the output in shared memory
+    if (priv_bytes <= 32u * 1024u) {
+        const uint64_t fb = (uint64_t)dtype_bytes(h->factor_dtype);
+        if (h->N <= 5 && h->dims[mode] <= (uint64_t)kHotTagMax && priv_bytes <= kHotBlockBytes &&
+            h->maxcount[mode] >= kSegHotMinCount && ((uint64_t)R * fb) % 16 == 0 && ((uint64_t)R * accb) % 16 == 0)
+            return RELATE_CONFLICT_SEGMENTED;
+        return RELATE_CONFLICT_PRIVATIZED;
+    }
     const double reuse = h->distinct[mode] ? (double)h->nnz / (double)h->distinct[mode] : 0.0;
     const double mean_run = h->runs_n[mode] ? (double)h->nnz / (double)h->runs_n[mode] : 0.0;
     // "minimum fiber reuse 8" (Sec. 4.1.3) for reduction-based synchronisation

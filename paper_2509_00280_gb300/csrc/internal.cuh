@@ -167,9 +167,16 @@ constexpr long long kWaitCycles = 4000000000LL;
 // Upper bound of hot (most populated) rows per mode kept in shared memory.
 constexpr int kHotMax = 256;
 // Global scratch of a handle for the SEGMENTED kernel's per-block copies of
-// the hot rows: 4 KB per block for up to 1024 blocks.
-constexpr size_t kHotBlockBytes = 4096;
+// the hot rows: 8 KB per block for up to 1024 blocks.
+constexpr size_t kHotBlockBytes = 8192;
 constexpr size_t kHotScratchBytes = 1024 * kHotBlockBytes;
+// Hot slots a 16-bit tile-order entry can tag (1 + slot in its top 5 bits).
+constexpr int kHotTagMax = 31;
+// A SEGMENTED mode keeps per-block copies of its hottest rows once its most
+// populated row has this many nonzeros (about one global FP32 addition per
+// tile holding the row): the random walk of 2^15 roundings, 2^-24 x
+// sqrt(2^15) relative, stays well below 1e-5.
+constexpr uint64_t kSegHotMinCount = 1u << 15;
 
 // Hot rows of one mode from its histogram: the kHotMax most populated rows
 // (ties by row id), most populated first; 0xffffffff pads modes with fewer

@@ -31,12 +31,6 @@ int max_dynamic_smem(const void *kern) {
     return lim;
 }
 
-// A SEGMENTED mode caches its hottest rows once its most populated row has
-// this many nonzeros (about one global FP32 addition per tile holding the
-// row): the random walk of 2^15 roundings, 2^-24 * sqrt(2^15) relative, stays
-// well below 1e-5.
-constexpr uint64_t kSegHotMinCount = 1u << 15;
-
 int mttkrp_acc_bytes(int factor_dtype) { return factor_dtype == RELATE_F64 ? 8 : 4; }
 
 cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int val_dtype, int smem_budget,
@@ -87,7 +81,7 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
         // so their flushes go straight to global memory. Runs are tagged
         // 0x80000000|slot, so the hot path needs rows < 2^31.
         // SEGMENTED tiles keep their hottest rows in per-block copies in
-        // global scratch (4 KB per block, no shared memory), and only in modes
+        // global scratch (8 KB per block, no shared memory), and only in modes
         // whose hottest row has enough nonzeros for its global additions to
         // matter.
         int hot = 0;

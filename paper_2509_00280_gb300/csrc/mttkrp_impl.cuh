@@ -142,6 +142,7 @@ constexpr int kTile = 2048;       // nonzeros per tile
 constexpr int kTileBits = 11;     // log2(kTile): a tile position in a tile-order entry
 static_assert((1 << kTileBits) == kTile, "tile positions take kTileBits bits");
 constexpr int kTagMax = (1 << (16 - kTileBits)) - 1;  // hot slots a 16-bit tile-order entry can tag
+static_assert(kTagMax == kHotTagMax, "the AUTO rule counts on the tag range");
 constexpr int kItems = kTile / kThreads;
 constexpr int kSortBins = 2048;   // widest row range a tile may span to be sorted
 constexpr int kSortBinBits = 11;  // log2(kSortBins): hashed bins take this many bits
