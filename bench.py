@@ -39,11 +39,11 @@ CPU_SAMPLE_NNZ = 5_000_000  # nonzeros of the workload the CPU oracle runs per s
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": "22c053f87afdcc7ae0fd3004a029b1f64534095ae431904f63ea727877d28dc2",
-               # 20M-nonzero capture (336.8 MB per launch), stream part (8-byte
+NCU_TRAFFIC = {"sha256": "b95f435e32cd5dd9716be6ae0ccdfb7600a6e49460af90a901e7ebb066b690b6",
+               # 20M-nonzero capture (336.9 MB per launch), stream part (8-byte
                # word, 4-byte value, 2-byte tile-order entry) scaled to 50M
-               # nonzeros: 336.8 MB + 30M x 14 B
-               "bytes_per_launch": 756.8e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
+               # nonzeros: 336.9 MB + 30M x 14 B
+               "bytes_per_launch": 756.9e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
 
 
 def _peaks():
