@@ -46,7 +46,7 @@ typedef enum {
                                            even after the ridge retry */
     RELATE_ERR_TIMEOUT = -7,            /* a bounded device wait ran out */
     RELATE_ERR_CUDA = -8,               /* CUDA runtime error; see relate_last_error() */
-    RELATE_ERR_UNSUPPORTED = -9         /* valid request this build does not handle */
+    RELATE_ERR_UNSUPPORTED = -9         /* valid request the library does not handle */
 } relate_status_t;
 
 typedef enum { RELATE_F64 = 0, RELATE_F32 = 1, RELATE_BF16 = 2 } relate_dtype_t;
