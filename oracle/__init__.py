@@ -245,6 +245,17 @@ def cholesky(V: np.ndarray) -> np.ndarray:
     return L
 
 
+def factor_normal(V: np.ndarray) -> tuple[np.ndarray, int]:
+    """Cholesky of the normal-equations matrix with the oracle's one ridge
+    retry (V + 1e-12 tr(V)/R I when V itself fails). Returns (L, ridged)."""
+    v = _c(V, np.float64)
+    R = v.shape[0]
+    L = np.zeros((R, R), dtype=np.float64)
+    ridged = ctypes.c_int(0)
+    _check(_load().orc_factor_normal(_p(v), R, _p(L), ctypes.byref(ridged)), "factor_normal")
+    return L, int(ridged.value)
+
+
 def solve_rows(M: np.ndarray, V: np.ndarray) -> np.ndarray:
     """A = M V^{-1} through the oracle's Cholesky (with ridge retry)."""
     m = _c(M, np.float64)

@@ -321,15 +321,17 @@ int orc_mttkrp(const uint32_t *coords, const double *vals, const uint64_t *dims,
 /* Dense CP-ALS remainder (standard ALS, Kolda & Bader, cited in Sec. 2.2) */
 /* ---------------------------------------------------------------------- */
 
-/* G = A^T A for A (I x R), plain triple loop. */
+/* G = A^T A for A (I x R), plain triple loop: G[r][s] = sum_i A[i][r] A[i][s],
+ * every entry summed over i in increasing order from 0. The rows are the
+ * outer loop so that A is read once, row by row. */
 void orc_gram(const double *A, uint64_t I, int R, double *G)
 {
-    for (int r = 0; r < R; r++)
-        for (int s = 0; s < R; s++) {
-            double acc = 0.0;
-            for (uint64_t i = 0; i < I; i++) acc += A[i * R + r] * A[i * R + s];
-            G[r * R + s] = acc;
-        }
+    for (int j = 0; j < R * R; j++) G[j] = 0.0;
+    for (uint64_t i = 0; i < I; i++) {
+        const double *a = A + i * R;
+        for (int r = 0; r < R; r++)
+            for (int s = 0; s < R; s++) G[r * R + s] += a[r] * a[s];
+    }
 }
 
 /* Textbook Cholesky V = L L^T (lower L, row-major R x R). Returns 0 on
@@ -445,13 +447,15 @@ int orc_cpals(const uint32_t *coords, const double *vals, const uint64_t *dims, 
             ridges += ridged;
             if (rc) goto out;
             orc_solve_rows(M, dims[n], R, L, factors[n]);
-            for (int r = 0; r < R; r++) {
-                double ss = 0.0;
-                for (uint64_t i = 0; i < dims[n]; i++) ss += factors[n][i * R + r] * factors[n][i * R + r];
-                lambda[r] = sqrt(ss);
-                if (lambda[r] > 0.0)
-                    for (uint64_t i = 0; i < dims[n]; i++) factors[n][i * R + r] /= lambda[r];
-            }
+            /* column 2-norms (each summed over i in increasing order), then
+             * every column with a nonzero norm divided by it */
+            for (int r = 0; r < R; r++) lambda[r] = 0.0;
+            for (uint64_t i = 0; i < dims[n]; i++)
+                for (int r = 0; r < R; r++) lambda[r] += factors[n][i * R + r] * factors[n][i * R + r];
+            for (int r = 0; r < R; r++) lambda[r] = sqrt(lambda[r]);
+            for (uint64_t i = 0; i < dims[n]; i++)
+                for (int r = 0; r < R; r++)
+                    if (lambda[r] > 0.0) factors[n][i * R + r] /= lambda[r];
             orc_gram(factors[n], dims[n], R, G + (size_t)n * R * R);
         }
         /* fit, with M = MTTKRP of the last mode and A_{N-1} normalised */

@@ -26,6 +26,77 @@ def test_gram_cholesky_solve():
         oracle.cholesky(-np.eye(3))
 
 
+def test_ridge_retry_on_a_singular_normal_matrix():
+    """The Hadamard product of Grams is positive semidefinite; it is singular
+    when a factor has a zero column or two equal columns, and then the first
+    Cholesky meets a zero pivot. The retry factors V + 1e-12 tr(V)/R I.
+    [[1,1],[1,1]] (B = [1 1], a repeated column): the second pivot is exactly
+    1 - 1 = 0. The ridge's scale is pinned by L L^T against V + ridge I at
+    1e-14, well below the ridge itself (1e-12); a ridge with the wrong sign
+    fails again (NOT_PD)."""
+    V = np.array([[1.0, 1.0], [1.0, 1.0]])
+    with pytest.raises(oracle.OracleError):
+        oracle.cholesky(V)
+    L, ridged = oracle.factor_normal(V)
+    assert ridged == 1
+    W = V + 1e-12 * np.trace(V) / 2 * np.eye(2)
+    assert np.abs(L @ L.T - W).max() <= 1e-14
+    assert np.abs(np.diag(L @ L.T - V) - 1e-12).max() <= 1e-14
+    # a V that factors at once takes no ridge
+    L0, r0 = oracle.factor_normal(np.array([[4.0, 2.0], [2.0, 3.0]]))
+    assert r0 == 0 and np.allclose(L0 @ L0.T, [[4.0, 2.0], [2.0, 3.0]], rtol=0, atol=1e-15)
+
+
+def test_ridge_retry_with_a_zero_factor_column_solves_the_ridged_system():
+    """A zero column r of a factor makes row and column r of V zero: the
+    pivot of column r is exactly 0, the retry succeeds, and the solve gives
+    A = M (V + ridge I)^{-1}; a right-hand side with a zero column r (the
+    MTTKRP of that factor) keeps column r of A exactly zero."""
+    rng = np.random.default_rng(27)
+    B = rng.random((60, 6))
+    B[:, 3] = 0.0
+    C = rng.random((50, 6))
+    V = (B.T @ B) * (C.T @ C)
+    assert np.all(V[3] == 0.0) and np.all(V[:, 3] == 0.0)
+    L, ridged = oracle.factor_normal(V)
+    assert ridged == 1
+    ridge = 1e-12 * np.trace(V) / 6
+    W = V + ridge * np.eye(6)
+    assert np.abs(L @ L.T - W).max() <= 1e-13 * np.abs(W).max()
+    assert abs(L[3, 3] ** 2 - ridge) <= 1e-12 * ridge and np.all(L[3, :3] == 0.0)
+    M = rng.standard_normal((40, 6))
+    M[:, 3] = 0.0
+    A = oracle.solve_rows(M, V)
+    assert np.all(A[:, 3] == 0.0)
+    assert np.linalg.norm(A @ W - M) <= 1e-12 * np.linalg.norm(M) * np.linalg.cond(W[np.ix_([0, 1, 2, 4, 5],
+                                                                                             [0, 1, 2, 4, 5])])
+    np.testing.assert_allclose(A, M @ np.linalg.inv(W), rtol=1e-9, atol=1e-12)
+
+
+def test_cpals_with_a_zero_initial_column_takes_the_ridge_every_mode():
+    """A zero column in one initial factor makes every mode's V singular in
+    the first sweep (the zero column propagates): the oracle counts one ridge
+    retry per mode and iteration, the zero column stays zero, and the other
+    columns follow the run without it within the ridge's perturbation."""
+    rng = np.random.default_rng(28)
+    dims = (30, 25, 20)
+    X = (rng.random(dims) < 0.2) * rng.random(dims)
+    c, v = _to_coo(X)
+    R, iters = 4, 3
+    init = [rng.random((d, R)) for d in dims]
+    init[2][:, 1] = 0.0
+    res = oracle.cpals(c, v, dims, R, iters, 0.0, init)
+    assert res["ridges"] == 3 * iters
+    for f in res["factors"]:
+        assert np.all(f[:, 1] == 0.0)
+    assert res["lam"][1] == 0.0
+    keep = [0, 2, 3]
+    ref = oracle.cpals(c, v, dims, 3, iters, 0.0, [f[:, keep] for f in init])
+    assert ref["ridges"] == 0
+    assert np.max(np.abs(res["fit_trace"] - ref["fit_trace"])) <= 1e-9
+    np.testing.assert_allclose(res["lam"][keep], ref["lam"], rtol=1e-8)
+
+
 def _cp_dense(lam, fs):
     N = len(fs)
     letters = "abcdefgh"[:N]
