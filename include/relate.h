@@ -175,14 +175,20 @@ typedef struct {
  *                 - 2 sum_r lambda_r <M(:,r), A_{N-1}(:,r)>)) / ||X||
  * and the loop stops when it > 1 and |fit - fit_prev| < tol, or after iters.
  * factors: host array of nmodes DEVICE pointers (handle's factor dtype),
- * in = initial factors, out = normalised factors. lambda: HOST, R doubles,
- * out. info: nullable. Runs on the handle's stream; synchronises once per
+ * in = initial factors, out = normalised factors. lambda: R doubles, out,
+ * HOST or DEVICE memory (the copy's direction follows from the unified
+ * address space); written when the call returns. info: nullable. Runs on the handle's stream; synchronises once per
  * iteration (the fit), or once per call in graph mode with tol <= 0
- * (relate_set_cpals_graph). Errors: INVALID_ARG, NOT_PD, OOM, TIMEOUT,
- * CUDA. */
+ * (relate_set_cpals_graph). TIMEOUT: a bounded device wait of the MTTKRP or
+ * of the tensor-core Gram (BF16 factors) ran out. Errors: INVALID_ARG,
+ * NOT_PD, OOM, TIMEOUT, CUDA. */
 int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *factors,
                  double *lambda, relate_cpals_info_t *info);
 
+/* Encoding statistics. l(n), l(p) and the bit order are those of Sec. 3.3
+ * (bit budget, Sec. 3.3.1-3.3.2 interleaving); runs / distinct / maxcount are
+ * the fiber statistics that pick the synchronisation per mode (the "minimum
+ * fiber reuse" rule of Sec. 4.1.3): fiber reuse = nnz / distinct. */
 typedef struct {
     int nmodes;
     int lp;                 /* l(p) */
@@ -199,7 +205,8 @@ typedef struct {
     int8_t bit_order[RELATE_MAX_KEY_BITS];
 } relate_stats_t;
 
-/* Encoding statistics (host struct filled from the handle). */
+/* Fills the HOST struct *s from the handle (no device work, no
+ * synchronisation). Errors: INVALID_ARG (NULL h or s). */
 int relate_get_stats(relate_handle_t h, relate_stats_t *s);
 
 /* Conflict strategy relate_mttkrp uses for `mode` at rank R (the AUTO rule
@@ -210,7 +217,10 @@ int relate_get_conflict(relate_handle_t h, int mode, int R, relate_conflict_t *o
 int relate_set_conflict(relate_handle_t h, int mode, relate_conflict_t c);
 
 /* Changes the factor / accumulation dtypes used by later calls
- * (F64/F64, F32/F32 or BF16/F32). */
+ * (F64/F64, F32/F32 or BF16/F32): the precision forms of the factors and of
+ * the MTTKRP accumulation; the encoding itself does not depend on them
+ * (storage of a linearized format depends only on the tensor, Sec. 4.2).
+ * Errors: INVALID_ARG (NULL h or another pair). */
 int relate_set_precision(relate_handle_t h, relate_dtype_t factor_dtype, relate_dtype_t acc_dtype);
 
 /* Changes the stream used by relate_cpals. */
@@ -256,38 +266,56 @@ int relate_release_cached_memory(void);
  * counterpart (launch overhead only). Errors: INVALID_ARG. */
 int relate_set_cpals_graph(relate_handle_t h, int enable);
 
-/* Copies the encoded stream out, in encoded (sorted) order, to DEVICE
- * buffers: coords_out N x nnz uint32 SoA (nullable), vals_out nnz values in
- * the val dtype (nullable), perm_out nnz uint32 original indices (nullable),
- * keys_out nnz x 2 uint64 (lo, hi) positions p (nullable). Async on stream. */
+/* Decodes the linearized tensor {<v_i, p_i>} ordered by p (Sec. 3.3; the
+ * inverse of the bit-level encoding of Sec. 3.3.1-3.3.2) to DEVICE buffers,
+ * in encoded (sorted) order: coords_out N x nnz uint32 SoA (nullable),
+ * vals_out nnz values in the val dtype (nullable), perm_out nnz uint32
+ * original indices (nullable), keys_out nnz x 2 uint64 (lo, hi) positions p
+ * (nullable). Buffers are caller-owned. Async on stream. Errors: INVALID_ARG
+ * (NULL h), CUDA. */
 int relate_decode(relate_handle_t h, uint32_t *coords_out, void *vals_out, uint32_t *perm_out,
                   uint64_t *keys_out, void *stream);
 
-/* Copies the partition bounds to DEVICE buffers lo/hi, partitions x N
- * uint32 each (row q, column n). Async on stream. */
+/* Copies the bounds of the equal-work partitions of the sorted stream
+ * (Sec. 4.2: workload balance of linearized formats; partition q covers
+ * nonzeros [qS, min((q+1)S, nnz))) to caller-owned DEVICE buffers lo/hi,
+ * partitions x N uint32 each (row q, column n = min / max of i_n over the
+ * partition). Async on stream. Errors: INVALID_ARG (NULL argument), CUDA. */
 int relate_get_partitions(relate_handle_t h, uint32_t *lo, uint32_t *hi, void *stream);
 
-/* G = A^T A (the Gram step of CP-ALS) for a DEVICE matrix A (I x R,
- * row-major, dtype F64/F32/BF16), written to DEVICE G (R x R FP64).
- * FP64 inputs accumulate in FP64; FP32 and BF16 inputs accumulate in FP32
- * within blocks of rows and in FP64 across blocks. Async on stream. */
+/* G = A^T A (the Gram step of CP-ALS, the standard ALS cited in Sec. 2.2)
+ * for a DEVICE matrix A (I x R, row-major, dtype F64/F32/BF16), written to
+ * DEVICE G (R x R FP64). FP64 inputs accumulate in FP64; FP32 and BF16 inputs
+ * accumulate in FP32 within blocks of rows and in FP64 across blocks. BF16
+ * inputs with R % 8 == 0 and a 16-byte aligned A run on the tensor cores;
+ * that path synchronises `stream` once to read the kernel's bounded-wait
+ * status. Otherwise asynchronous on stream. Errors: INVALID_ARG, OOM,
+ * TIMEOUT (a tensor-core wait ran out; G is then NaN), CUDA. */
 int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream);
 
 /* The same Gram step as relate_gram, for callers that cannot allocate device
- * memory when they call it (e.g. inside a host callback enqueued on a stream,
- * or with all device memory already handed to their own pool): the per-block
- * partial sums live in a fixed 5.06 MB array compiled into the library
- * instead of a per-call allocation. The paper has no counterpart; this is a
- * deployment variant of the Gram step of CP-ALS.
+ * memory when they call it: applications that hand all device memory to
+ * their own pool up front, where one more allocation would fail or fragment
+ * it, and loops that cannot afford an allocator call that may synchronise the
+ * device. The per-block partial sums live in a fixed 5.06 MB array compiled
+ * into the library instead of a per-call allocation; every GPU that loads
+ * the library holds it until the process exits. The paper has no
+ * counterpart; this is a deployment variant of the Gram step of CP-ALS.
  * A, G, R, dtype, stream: as for relate_gram (A DEVICE I x R row-major, G
  * DEVICE R x R FP64). R outside [1, 64] is rejected (RELATE_ERR_INVALID_ARG)
  * because the array holds the partials of at most 64 columns.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before capturing
- * any stream work. Calls on one device share the array, so calls whose
- * kernels may overlap on the GPU (unordered streams) race and must be
- * serialised by the caller. Nothing needs clearing between calls: each call
- * writes every partial it reads. Allocates nothing; asynchronous on stream. */
+ * The first call on a device (and the first in a new CUDA context of it)
+ * looks up the array's device address with that device current; make that
+ * first call before capturing any stream work. Calls on one device share the
+ * array, so calls whose kernels may overlap on the GPU (unordered streams)
+ * race and must be serialised by the caller. Each call writes every partial
+ * it reads and clears the one status word it needs at zero. Like every CUDA
+ * call, it must not be made from a stream callback or a cudaLaunchHostFunc
+ * function. Allocates nothing; asynchronous on stream, except that the
+ * tensor-core path (BF16, R % 8 == 0, 16-byte aligned A) synchronises it once
+ * to read the kernel's bounded-wait status. Errors: INVALID_ARG, TIMEOUT (a
+ * tensor-core wait ran out; G is then NaN), UNSUPPORTED (device ordinal >=
+ * 64), CUDA. */
 int relate_gram_noalloc(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream);
 
 /* Synchronises `stream` and reports whether any kernel of this handle gave
@@ -298,16 +326,22 @@ int relate_gram_noalloc(const void *A, int64_t I, int R, relate_dtype_t dtype, d
  * Test hook (environment variable, read at each call): RELATE_FAULT=alloc
  * makes every library allocation fail (RELATE_ERR_OOM); RELATE_FAULT=timeout
  * makes every MTTKRP launch skip its first tile copy with a ~50 ms wait limit,
- * so that its bounded wait runs out and this call reports the timeout. */
+ * so that its bounded wait runs out and this call reports the timeout;
+ * RELATE_FAULT=gram_timeout makes every tensor-core Gram issue no MMA, with
+ * the same short limit on its waits. After a real (not injected) timeout the
+ * copies or tensor-core operations the kernel gave up on may still complete
+ * later: do not reuse the handle or its buffers; tear down the CUDA context. */
 int relate_sync_status(relate_handle_t h, void *stream);
 
-/* Frees the handle and all its device memory (synchronises its stream and
- * its second stream, not the device). The memory returns to the library's
- * pool (see relate_release_cached_memory). Work that uses the handle on
- * other streams must be complete. */
+/* Frees the handle and all its device memory, the encoding built by
+ * relate_encode (Sec. 3.3) and the CP-ALS workspace (synchronises its stream
+ * and its second stream, not the device). The memory returns to the
+ * library's pool (see relate_release_cached_memory). Work that uses the
+ * handle on other streams must be complete. NULL is ignored. */
 void relate_free(relate_handle_t h);
 
-/* Static description of a status code. */
+/* Static description of a status code (the codes above; the paper defines
+ * none). Never NULL; the string must not be freed. */
 const char *relate_status_string(int status);
 
 /* Message of the last error on this host thread ("" if none). */

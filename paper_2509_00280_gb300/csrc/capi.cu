@@ -71,10 +71,20 @@ cudaError_t lib_pool(cudaMemPool_t *out) {
 // Test hook: RELATE_FAULT=alloc makes every library allocation fail (as if
 // the device were out of memory); RELATE_FAULT=timeout makes every MTTKRP
 // launch skip its first tile copy with a 1e8-cycle wait limit, so that the
-// bounded wait runs out and the launch reports a timeout. Unset in normal use.
+// bounded wait runs out and the launch reports a timeout;
+// RELATE_FAULT=gram_timeout makes every tensor-core Gram issue no MMA, with
+// the same short limit on its waits for their completion. Unset in normal use.
 bool fault_is(const char *what) {
     const char *f = getenv("RELATE_FAULT");
     return f && strcmp(f, what) == 0;
+}
+
+// launch_gram with the gram_timeout test hook applied; a tensor-core wait
+// that runs out sets bit 1 of *err.
+cudaError_t gram_checked(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, int *err,
+                         cudaStream_t st) {
+    const bool f = fault_is("gram_timeout");
+    return launch_gram(A, I, R, dtype, scratch, G, err, st, f ? 100000000LL : 0, f ? 1 : 0);
 }
 
 template <typename T>
@@ -147,6 +157,8 @@ int set_last_error(int status, const char *msg) {
     snprintf(g_err, sizeof(g_err), "%s", msg ? msg : "");
     return status;
 }
+// The RELATE_FAULT test hook, for entry points in other translation units.
+bool fault_injected(const char *what) { return fault_is(what); }
 }  // namespace relate
 
 struct relate_handle_s {
@@ -466,7 +478,7 @@ int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_f
             if ((e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
                 (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
                                         st)) != cudaSuccess ||
-                (e = launch_gram(factors[n], In, R, RELATE_BF16, h->d_scratch, h->d_G + n * RR, st)) !=
+                (e = gram_checked(factors[n], In, R, RELATE_BF16, h->d_scratch, h->d_G + n * RR, h->d_err, st)) !=
                     cudaSuccess ||
                 (e = launch_inner_from_gram(h->d_V, h->d_G + n * RR, h->d_lambda, R, h->d_inner, st)) !=
                     cudaSuccess)
@@ -844,8 +856,8 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_status, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "relate_cpals: setup");
     for (int k = 0; k < N; k++)
-        if ((e = launch_gram(factors[k], (int64_t)h->dims[k], R, h->factor_dtype, h->d_scratch, h->d_G + k * RR, st)) !=
-            cudaSuccess)
+        if ((e = gram_checked(factors[k], (int64_t)h->dims[k], R, h->factor_dtype, h->d_scratch, h->d_G + k * RR,
+                              h->d_err, st)) != cudaSuccess)
             return cuda_fail(e, "relate_cpals: initial Gram");
     double prev = 0.0, fit = 0.0;
     int done = 0;
@@ -976,7 +988,9 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
         prev = fit;
     }
     if (gexec) cudaGraphExecDestroy(gexec);
-    if ((e = cudaMemcpyAsync(lambda, h->d_lambda, sizeof(double) * R, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+    // lambda may be host or device memory: the copy's direction follows from
+    // the unified address space
+    if ((e = cudaMemcpyAsync(lambda, h->d_lambda, sizeof(double) * R, cudaMemcpyDefault, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals: lambda to host");
     rc = hstatus[1] ? fail(RELATE_ERR_NOT_PD, "relate_cpals: normal equations not positive definite") : RELATE_OK;
@@ -1138,10 +1152,19 @@ int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G
     void *scratch = nullptr;
     cudaError_t e = dalloc(&scratch, dense_scratch_doubles(R) * 8, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_gram: scratch");
-    e = launch_gram(A, I, R, dtype, (double *)scratch, G, st);
+    int *err = gram_err_word((double *)scratch);
+    const bool tc = I > 0 && gram_uses_tc(A, R, dtype);
+    int flag = 0;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), st)) == cudaSuccess &&
+        (e = gram_checked(A, I, R, dtype, (double *)scratch, G, err, st)) == cudaSuccess && tc) {
+        // the tensor-core kernel reports a given-up wait in the status word
+        if ((e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+    }
     cudaError_t e2 = cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_gram: launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "relate_gram: free");
+    if (flag) return fail(RELATE_ERR_TIMEOUT, "relate_gram: a bounded tensor-core wait timed out (G is NaN)");
     return RELATE_OK;
 }
 

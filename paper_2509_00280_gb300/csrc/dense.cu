@@ -501,15 +501,24 @@ size_t dense_scratch_doubles(int R) {
     return (size_t)GR_BLOCKS * MAXPAIRS + (size_t)GR_BLOCKS * MAXR + 64;
 }
 
-cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, cudaStream_t st) {
+int *gram_err_word(double *scratch) {
+    return reinterpret_cast<int *>(scratch + (size_t)GR_BLOCKS * MAXPAIRS + (size_t)GR_BLOCKS * MAXR);
+}
+
+bool gram_uses_tc(const void *A, int R, int dtype) {
+    return dtype == RELATE_BF16 && gram_tc_supported(R) && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
+}
+
+cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, int *err,
+                        cudaStream_t st, long long wait_cycles, int fault_skip) {
     if (R < 1 || R > MAXR) return cudaErrorInvalidValue;
     if (I == 0) return cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
-    const int npairs_tc = R * (R + 1) / 2;
-    if (dtype == RELATE_BF16 && gram_tc_supported(R) && (reinterpret_cast<uintptr_t>(A) % 16) == 0) {
+    if (gram_uses_tc(A, R, dtype)) {
         // BF16 inputs: tcgen05 tensor cores, FP32 accumulation per block
-        int *err = reinterpret_cast<int *>(scratch + (size_t)GR_BLOCKS * MAXPAIRS + (size_t)GR_BLOCKS * MAXR);
+        const int npairs_tc = R * (R + 1) / 2;
         const int g = gram_tc_blocks(I);
-        cudaError_t e = launch_gram_tc((const __nv_bfloat16 *)A, I, R, scratch, err, st);
+        cudaError_t e = launch_gram_tc((const __nv_bfloat16 *)A, I, R, scratch, err ? err : gram_err_word(scratch),
+                                       wait_cycles, fault_skip, st);
         if (e != cudaSuccess) return e;
         k_gram_reduce<<<(npairs_tc + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(scratch, g, R, G);
         return cudaGetLastError();

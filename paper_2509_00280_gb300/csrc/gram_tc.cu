@@ -60,12 +60,12 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait (kWaitCycles SM clock cycles); false when it gave up.
-__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity) {
+// Bounded wait (`limit` SM clock cycles); false when it gave up.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity, long long limit) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -95,9 +95,12 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 
 // Per-block upper-triangle partials (FP64) of A^T A, A BF16 I x R (R <= 64,
-// R % 8 == 0 so a row is a whole number of 16-byte vectors).
+// R % 8 == 0 so a row is a whole number of 16-byte vectors). Every wait on a
+// commit gives up after wait_cycles; fault_skip (a test hook) issues no MMA
+// and no commit, so nothing is in flight when those waits run out.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const __nv_bfloat16 *__restrict__ A, int64_t I, int R,
-                                                           double *__restrict__ partial, int *__restrict__ err) {
+                                                           double *__restrict__ partial, int *__restrict__ err,
+                                                           long long wait_cycles, int fault_skip) {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_base;
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const __nv_bfloat16 *
         const int b = s & 1;
         unsigned char *buf = smem_tc + (size_t)b * TC_STAGE_BYTES;
         if (issued[b]) {  // the MMAs that read this buffer two stages ago are done
-            const bool ok = mbar_wait_limit(&bar[b], phase[b]);
+            const bool ok = mbar_wait_limit(&bar[b], phase[b], wait_cycles);
             phase[b] ^= 1;
             issued[b] = 0;
             if (__syncthreads_or(!ok)) {
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const __nv_bfloat16 *
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !fault_skip) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int cc = 0; cc < TC_CHUNKS; cc++) {
                 const uint32_t a_addr = saddr(buf + (size_t)cc * TC_CHUNK_BYTES);
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const __nv_bfloat16 *
     // all MMAs of this block are complete once both buffers' last commits land
     bool all_ok = true;
     for (int b = 0; b < 2; b++)
-        if (issued[b]) all_ok &= mbar_wait_limit(&bar[b], phase[b]);
+        if (issued[b]) all_ok &= mbar_wait_limit(&bar[b], phase[b], wait_cycles);
     if (__syncthreads_or(!all_ok) && tid == 0) gave_up = 1;
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -220,12 +223,14 @@ int gram_tc_blocks(int64_t I) {
     return (int)g;
 }
 
-cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err, cudaStream_t st) {
+cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err, long long wait_cycles,
+                           int fault_skip, cudaStream_t st) {
     const int g = gram_tc_blocks(I);
     const size_t smem = 2 * (size_t)TC_STAGE_BYTES;
     cudaError_t e = allow_max_dynamic_smem(k_gram_tc);
     if (e != cudaSuccess) return e;
-    k_gram_tc<<<g, TC_THREADS, smem, st>>>(A, I, R, partial, err);
+    k_gram_tc<<<g, TC_THREADS, smem, st>>>(A, I, R, partial, err, wait_cycles > 0 ? wait_cycles : kWaitCycles,
+                                           fault_skip);
     return cudaGetLastError();
 }
 

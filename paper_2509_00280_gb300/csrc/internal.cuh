@@ -201,16 +201,23 @@ int mttkrp_acc_bytes(int factor_dtype);
 // the row passes.
 size_t dense_scratch_doubles(int R);
 
-// G = A^T A, FP64 out (R x R) via per-block partials in `scratch`.
-cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G,
-                        cudaStream_t st);
+// G = A^T A, FP64 out (R x R) via per-block partials in `scratch`. BF16
+// inputs (gram_uses_tc) run on the tensor cores, whose bounded waits report a
+// timeout as *err |= 2 (err = null: the status word inside `scratch`,
+// gram_err_word) and NaN partials; wait_cycles <= 0 = kWaitCycles;
+// fault_skip (a test hook) issues no tensor-core work, so the waits run out.
+cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, int *err,
+                        cudaStream_t st, long long wait_cycles = 0, int fault_skip = 0);
+bool gram_uses_tc(const void *A, int R, int dtype);
+int *gram_err_word(double *scratch);
 
 // Tensor-core Gram partials for BF16 A (R % 8 == 0, R <= 64): one FP64
 // upper-triangle partial per block (gram_tc_blocks(I) blocks); err |= 2 and
 // NaN partials if a bounded wait on the tensor cores gave up.
 bool gram_tc_supported(int R);
 int gram_tc_blocks(int64_t I);
-cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err, cudaStream_t st);
+cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err,
+                           long long wait_cycles, int fault_skip, cudaStream_t st);
 
 // V = Hadamard_{k != n} G_k (kept in Vsave); FP64 Cholesky; V^{-1} in FP64
 // (f64_apply) or FP32 (Vinv32, always written).

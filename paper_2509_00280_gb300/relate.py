@@ -221,15 +221,18 @@ def relate_mttkrp(h: Handle, mode: int, factors, R: int, out, stream=None) -> No
                                _stream(stream)), "relate_mttkrp")
 
 
-def relate_cpals(h: Handle, R: int, iters: int, tol: float, factors):
-    """Runs CP-ALS in place on `factors` (device tensors). Returns
-    dict(lam (numpy), fit, iters, status, ridge_retries, fit_trace)."""
-    lam = np.zeros(R, dtype=np.float64)
+def relate_cpals(h: Handle, R: int, iters: int, tol: float, factors, lam=None):
+    """Runs CP-ALS in place on `factors` (device tensors). `lam`: optional
+    output for lambda (R float64, a host numpy array or a CUDA tensor); a
+    host array is made if None. Returns dict(lam, fit, iters, status,
+    ridge_retries, fit_trace)."""
+    if lam is None:
+        lam = np.zeros(R, dtype=np.float64)
     trace = np.zeros(max(iters, 1), dtype=np.float64)
     info = CpalsInfo()
     info.fit_trace = trace.ctypes.data
     rc = lib().relate_cpals(h.raw, int(R), int(iters), float(tol), _ptr_array(factors, h.nmodes),
-                            lam.ctypes.data, ctypes.byref(info))
+                            _ptr(lam), ctypes.byref(info))
     _check(rc, "relate_cpals")
     return {"lam": lam, "fit": info.fit, "iters": info.iters, "status": info.status,
             "ridge_retries": info.ridge_retries, "fit_trace": trace[:info.iters].copy()}

@@ -115,3 +115,53 @@ def test_not_positive_definite_reported_in_both_graph_paths():
         for tol in (0.0, 1e-6):
             res = _graph_run(c, v, dims, 4, 5, tol, init, graph)
             assert res.get("error") == -6, (graph, tol, res)  # RELATE_ERR_NOT_PD
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_ridge_retry_path_matches_the_oracle(graph):
+    """A zero column in one initial factor makes the normal-equations matrix
+    of every mode singular (a zero pivot): the first Cholesky fails and the
+    retry with V + 1e-12 tr(V)/R I succeeds, once per mode and iteration,
+    on the GPU as in the oracle. Retry count, fit trace (<= 1e-9), lambda
+    and factors are compared; the zero column stays exactly zero."""
+    rng = np.random.default_rng(29)
+    dims = (300, 250, 200)
+    nnz = 20000
+    c = np.stack([rng.integers(0, d, nnz) for d in dims]).astype(np.uint32)
+    v = rng.random(nnz)
+    R, iters = 6, 4
+    init = [rng.random((d, R)) for d in dims]
+    init[2][:, 1] = 0.0
+    ref = oracle.cpals(c, v, dims, R, iters, 0.0, init)
+    assert ref["ridges"] == 3 * iters
+    s = torch.cuda.Stream()
+    h = encode_dev(c, v, dims, factor_dtype="f64", stream=s)
+    rl.relate_set_cpals_graph(h, graph)
+    dfs = factors_dev(init, "f64")
+    torch.cuda.synchronize()
+    res = rl.relate_cpals(h, R, iters, 0.0, dfs)
+    h.close()
+    assert res["status"] == 0 and res["iters"] == iters
+    assert res["ridge_retries"] == ref["ridges"]
+    assert np.max(np.abs(res["fit_trace"] - ref["fit_trace"])) <= 1e-9
+    np.testing.assert_allclose(res["lam"], ref["lam"], rtol=1e-7, atol=0)
+    for f, g in zip(dfs, ref["factors"]):
+        f = f.cpu().numpy()
+        assert np.all(f[:, 1] == 0.0)
+        assert np.linalg.norm(f - g) <= 1e-6 * np.linalg.norm(g)
+
+
+def test_lambda_to_device_memory():
+    """relate_cpals writes lambda to a device buffer as well as to a host one."""
+    spec = synth.scaled(synth.WORKLOADS["uniform3d-1000x1000x1000-1M"]["spec"], 30_000, dims=(90, 80, 70))
+    c, v = synth.make_tensor(spec)
+    fs = synth.init_factors(spec.dims, 5, seed=0)
+    out = []
+    for lam in (None, torch.full((5,), float("nan"), dtype=torch.float64, device=DEV)):
+        h = encode_dev(c, v, spec.dims, factor_dtype="f64")
+        res = rl.relate_cpals(h, 5, 3, 0.0, factors_dev(fs, "f64"), lam=lam)
+        h.close()
+        got = res["lam"]
+        out.append(got.cpu().numpy() if hasattr(got, "cpu") else got)
+    assert np.all(np.isfinite(out[1]))
+    np.testing.assert_allclose(out[1], out[0], rtol=1e-10, atol=0)  # atomics order differs between runs

@@ -9,6 +9,10 @@ RELATE_FAULT is the library's host-side test hook:
   handle's error flag and returns, and the host reads RELATE_ERR_TIMEOUT
   (relate_sync_status, relate_cpals). No trap, no fault: the context stays
   usable and the next MTTKRP (hook unset) matches the oracle.
+* "gram_timeout": the tensor-core Gram (BF16 factors) issues no MMA and
+  waits for their completion with the same short limit; relate_gram and
+  relate_cpals report RELATE_ERR_TIMEOUT, and with the hook unset the same
+  calls succeed.
 """
 import numpy as np
 import pytest
@@ -62,4 +66,28 @@ def test_injected_timeout_is_reported_and_the_context_stays_usable(monkeypatch):
     rl.relate_sync_status(h)
     ref = oracle.mttkrp(c, v.astype(np.float64), spec.dims, 0, [f.astype(np.float64) for f in fs])
     assert rel_fro(mttkrp_dev(h, 0, dfs, R), ref) <= 1e-5
+    h.close()
+
+
+def test_injected_tensor_core_gram_timeout_is_reported(monkeypatch):
+    rng = np.random.default_rng(31)
+    A = torch.from_numpy(rng.random((20000, 32))).to("cuda").to(torch.bfloat16).contiguous()
+    G = torch.empty((32, 32), dtype=torch.float64, device="cuda")
+    monkeypatch.setenv("RELATE_FAULT", "gram_timeout")
+    with pytest.raises(rl.RelateError) as ei:
+        rl.relate_gram(A, 32, "bf16", G)
+    assert ei.value.status == TIMEOUT
+    spec, c, v = _small()
+    fs = synth.init_factors(spec.dims, 16, seed=0, dtype=np.float32)
+    h = encode_dev(c, v, spec.dims, factor_dtype="bf16")
+    with pytest.raises(rl.RelateError) as ei:
+        rl.relate_cpals(h, 16, 2, 0.0, factors_dev(fs, "bf16"))
+    assert ei.value.status == TIMEOUT
+    monkeypatch.delenv("RELATE_FAULT")
+    rl.relate_gram(A, 32, "bf16", G)
+    torch.cuda.synchronize()
+    exact = A.to(torch.float64).T @ A.to(torch.float64)
+    assert float(torch.linalg.norm(G - exact) / torch.linalg.norm(exact)) <= 2e-5
+    res = rl.relate_cpals(h, 16, 2, 0.0, factors_dev(fs, "bf16"))
+    assert res["status"] == 0 and np.isfinite(res["fit"])
     h.close()

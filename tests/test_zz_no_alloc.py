@@ -1,11 +1,11 @@
 """relate_gram_noalloc against relate_gram.
 
 relate_gram_noalloc serves callers that cannot allocate device memory when
-they compute a Gram matrix (a host callback on a stream, or an application
-whose device memory already belongs to its own pool): its partial sums live
-in a fixed array inside the library. This file is collected last so that a
-run stopping at the first failure has already run every other test; it also
-passes on its own in a fresh process.
+they compute a Gram matrix (an application whose device memory already
+belongs to its own pool, or a loop that cannot afford an allocator call): its
+partial sums live in a fixed array inside the library. This file is collected
+last so that a run stopping at the first failure has already run every other
+test; it also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
@@ -51,3 +51,25 @@ def test_noalloc_gram_rejects_rank_beyond_the_fixed_scratch():
     with pytest.raises(rl.RelateError) as ei:
         rl.relate_gram_noalloc(A, 65, "f32", G)
     assert ei.value.status == -1 and "[1, 64]" in str(ei.value)
+
+
+def test_noalloc_gram_reports_a_tensor_core_timeout_and_recovers(monkeypatch):
+    """The tensor-core path's bounded-wait status word lives in the shared
+    array: a timed-out call (RELATE_FAULT=gram_timeout issues no MMA, so the
+    waits run out) returns RELATE_ERR_TIMEOUT, and the next call, which
+    clears the word first, succeeds and matches relate_gram."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(78)
+    A = torch.from_numpy(rng.random((50_000, 64))).to(dev).to(torch.bfloat16).contiguous()
+    G = torch.empty((64, 64), dtype=torch.float64, device=dev)
+    monkeypatch.setenv("RELATE_FAULT", "gram_timeout")
+    with pytest.raises(rl.RelateError) as ei:
+        rl.relate_gram_noalloc(A, 64, "bf16", G)
+    assert ei.value.status == -7
+    monkeypatch.delenv("RELATE_FAULT")
+    G_ref = torch.empty((64, 64), dtype=torch.float64, device=dev)
+    rl.relate_gram(A, 64, "bf16", G_ref)
+    rl.relate_gram_noalloc(A, 64, "bf16", G)
+    torch.cuda.synchronize()
+    assert torch.isfinite(G).all()
+    assert _rel(G, G_ref) <= TOL["bf16"]
