@@ -5,6 +5,11 @@ relate_encode (GPU key build, radix sort, partitions, statistics) followed by
 relate_cpals for the workload's iteration count (MTTKRP of every mode, FP64
 normal equations, normalisation, fit) from the same initial factors.
 
+Default: the 4-mode 150M-nonzero workload (5M x 1M x 100K x 24, R = 64, 10
+iterations) with FP64 factors and accumulation, the paper's precision
+(Sec. 4.1.3); the FP32 and BF16 factor forms of the same workload are timed
+after it and reported under "variants".
+
 value = MTTKRP work of the step (nnz * R * N * iterations) / step time,
 summed over ranks (replicas, weak scaling) and divided by the slowest rank's
 time. e2e = the same through the C ABI with host buffers: pinned host
@@ -12,7 +17,7 @@ coordinates, values and factors copied in and the factors and lambda copied
 out inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-       [--workload NAME] [--factor-dtype f32|bf16|f64]
+       [--workload NAME] [--factor-dtype f64|f32|bf16] [--variants f32,bf16]
 """
 from __future__ import annotations
 
@@ -31,10 +36,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "zipf3d-200Kx200Kx5K-50M"
+DEFAULT_WORKLOAD = "zipf4d-5Mx1Mx100Kx24-150M"
+DEFAULT_FACTOR_DTYPE = "f64"  # the paper's precision (Sec. 4.1.3)
+DEFAULT_VARIANTS = "f32,bf16"
 METRIC = "MTTKRP nnz*R/s (all modes, whole CP-ALS job)"
 UNIT = "nnz*R/s"
-CPU_SAMPLE_NNZ = 5_000_000  # nonzeros of the workload the CPU oracle runs per step
+CPU_SAMPLE_NNZ = 30_000_000    # nonzeros of the workload the OpenMP CPU baseline sweeps
+CPU_SINGLE_NNZ = 1_000_000     # nonzeros the single-threaded oracle sweeps (reported beside it)
+REF_SAMPLE_NNZ = 10_000_000    # nonzeros per step of the --impl reference arm
+# FP64 issue rate of a GB300 SM: 2 FP64 FMA per clock (a register-only FMA
+# loop measures 626 G FMA/s on 152 SMs at 2070 MHz, 1.99 per SM per clock)
+FP64_FMA_PER_SM_CLK = 2
+NUM_SMS = 152
 
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
@@ -53,6 +66,19 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _fp64_peak_tflops():
+    """FP64 arithmetic peak from unit counts and the clock: 152 SMs x 2 FMA
+    (4 flops) per SM per clock x the maximum SM clock (MEASURED_PEAKS.json's
+    sm_max_mhz, else 2070 MHz) = 1.26 TFLOP/s, the nominal 1.25."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return NUM_SMS * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
 
 
 def _kernel_sha() -> str:
@@ -189,20 +215,160 @@ def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
     return encode + cpals
 
 
-def run_cpu_reference(args, w, coords, vals, sample_nnz: int, iters: int = 1):
-    """The oracle as it stands (single-threaded C, FP64) on a bounded sample
-    of the same workload: CP-ALS iterations on the first sample_nnz nonzeros."""
+def _host_cores():
+    """Threads the CPU legs use: the cores this process may run on."""
+    try:
+        aff = sorted(os.sched_getaffinity(0))
+    except Exception:
+        aff = list(range(os.cpu_count() or 1))
+    return len(aff), aff
+
+
+def _affinity_str(aff) -> str:
+    if not aff:
+        return ""
+    runs, a = [], aff[0]
+    prev = a
+    for x in aff[1:] + [None]:
+        if x is not None and x == prev + 1:
+            prev = x
+            continue
+        runs.append(f"{a}-{prev}" if prev != a else f"{a}")
+        if x is not None:
+            a = prev = x
+    return ",".join(runs)
+
+
+def _cpu_sweep(coords, vals, dims, factors, nthreads, sweeps):
+    """Median time of `sweeps` all-mode MTTKRP sweeps of the oracle's OpenMP
+    build (oracle_omp.c) on nthreads threads."""
     import oracle
-    spec = w["spec"]
-    R = w["R"]
-    c = np.ascontiguousarray(coords[:, :sample_nnz])
-    v = vals[:sample_nnz].astype(np.float64)
-    fs = __import__("synth").init_factors(spec.dims, R, seed=0)
+    outs = [np.empty((int(d), factors[0].shape[1]), dtype=np.float64) for d in dims]
+    oracle.mttkrp_omp(coords[:, :1000], vals[:1000], dims, 0, factors, nthreads, out=outs[0])  # load, warm
+    times = []
+    for _ in range(sweeps):
+        t0 = time.perf_counter()
+        for n in range(len(dims)):
+            oracle.mttkrp_omp(coords, vals, dims, n, factors, nthreads, out=outs[n])
+        times.append(time.perf_counter() - t0)
+    return statistics.median(times)
+
+
+def cpu_baseline(w, coords, vals):
+    """The oracle's MTTKRP on the host cores: the OpenMP build on every core
+    this process may use (all-mode sweeps, median of 3, on the first
+    CPU_SAMPLE_NNZ nonzeros), and the plain single-threaded compensated
+    oracle (one all-mode sweep on the first CPU_SINGLE_NNZ nonzeros)."""
+    import oracle
+    import synth
+    spec, R = w["spec"], w["R"]
+    N = len(spec.dims)
+    fs = synth.init_factors(spec.dims, R, seed=0)
+    cores, aff = _host_cores()
+    n_omp = min(spec.nnz, CPU_SAMPLE_NNZ)
+    c = np.ascontiguousarray(coords[:, :n_omp])
+    v = vals[:n_omp].astype(np.float64)
+    dt = _cpu_sweep(c, v, spec.dims, fs, cores, 3)
+    omp_val = n_omp * R * N / dt
+    n1 = min(spec.nnz, CPU_SINGLE_NNZ)
+    c1 = np.ascontiguousarray(coords[:, :n1])
+    v1 = vals[:n1].astype(np.float64)
     t0 = time.perf_counter()
-    oracle.cpals(c, v, spec.dims, R, iters, 0.0, fs)
-    dt = time.perf_counter() - t0
-    units = sample_nnz * R * len(spec.dims) * iters
-    return (units / dt if iters else 0.0), dt
+    for n in range(N):
+        oracle.mttkrp(c1, v1, spec.dims, n, fs)
+    dt1 = time.perf_counter() - t0
+    return {"value": omp_val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_omp} nonzeros of {spec.name} (R = {R}), all {N} modes per sweep, median of 3 "
+                      f"sweeps ({dt:.2f} s each): OpenMP build of the oracle MTTKRP (oracle_omp.c, FP64) on "
+                      f"{cores} threads",
+            "nproc": os.cpu_count(), "affinity": _affinity_str(aff),
+            "single_thread": {"value": n1 * R * N / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"first {n1} nonzeros, one all-mode sweep of the compensated "
+                                        f"single-threaded oracle (oracle.c), {dt1:.2f} s"}}
+
+
+def run_reference(args, w, coords, vals, world):
+    """--impl reference: the oracle's MTTKRP (OpenMP build, FP64, every core
+    this process may use) on a bounded sample of the same workload; a step is
+    one all-mode MTTKRP sweep over the first REF_SAMPLE_NNZ nonzeros."""
+    import synth
+    spec, R = w["spec"], w["R"]
+    N = len(spec.dims)
+    cores, aff = _host_cores()
+    n = min(spec.nnz, REF_SAMPLE_NNZ)
+    c = np.ascontiguousarray(coords[:, :n])
+    v = vals[:n].astype(np.float64)
+    fs = synth.init_factors(spec.dims, R, seed=0)
+    for _ in range(args.warmup):
+        _cpu_sweep(c[:, :100_000], v[:100_000], spec.dims, fs, cores, 1)
+    times = []
+    for _ in range(args.steps):
+        times.append(_cpu_sweep(c, v, spec.dims, fs, cores, 1))
+    total = sum(times)
+    val = n * R * N * args.steps / total
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": spec.nnz, "R": R,
+                                            "sample_nnz": n, "step": "one all-mode MTTKRP sweep of the sample"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {n} nonzeros of {spec.name}, one all-mode MTTKRP sweep per step, "
+                                       f"OpenMP build of the oracle (oracle_omp.c, FP64) on {cores} threads",
+                             "nproc": os.cpu_count(), "affinity": _affinity_str(aff)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def _time_kernels(rl, torch, h, stream, d_fac, spec, R, fdt, dev, reps):
+    """Per-mode MTTKRP launch times (CUDA events on the launching stream, L2
+    flushed by a 256 MB write before each launch) with their algorithmic
+    bytes and flops."""
+    N = len(spec.dims)
+    stats = rl.relate_get_stats(h)
+    accdt = torch.float64 if fdt == "f64" else torch.float32
+    fb = {"f64": 8, "f32": 4, "bf16": 2}[fdt]
+    ab = 8 if fdt == "f64" else 4
+    vb = 8 if fdt == "f64" else 4
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    per_mode = []
+    for n in range(N):
+        out = torch.empty((spec.dims[n], R), dtype=accdt, device=dev)
+        ms = []
+        for r in range(reps + 1):
+            flush.fill_(float(r))  # 256 MB write evicts L2 between launches
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rl.relate_mttkrp(h, n, d_fac, R, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ms.append(e0.elapsed_time(e1))
+        per_mode.append({"mode": n, "ms": statistics.mean(ms), "alg_bytes": _algorithmic_bytes(stats, n, R, fb, ab, vb),
+                         "alg_flops": spec.nnz * R * N, "strategy": rl.relate_get_conflict(h, n, R)})
+    return stats, per_mode
+
+
+def _roofline(per_mode, fdt, workload):
+    """Roofline of the MTTKRP kernel over all modes: FP64 factors are bound by
+    the FP64 pipe (flops = nnz * R * N per launch against the FP64 peak), FP32
+    and BF16 factors against the measured HBM copy bandwidth (algorithmic
+    bytes per launch)."""
+    N = len(per_mode)
+    ms_total = sum(m["ms"] for m in per_mode)
+    peak_hbm, kind = _peaks()
+    gbs = sum(m["alg_bytes"] for m in per_mode) / (ms_total / 1000.0) / 1e9
+    hbm = {"achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": gbs / peak_hbm, "peak_kind": kind}
+    traffic = None
+    if NCU_TRAFFIC["sha256"] == _kernel_sha() and NCU_TRAFFIC["workload"] == workload and \
+            NCU_TRAFFIC.get("dtype", "f32") == fdt:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    if fdt == "f64":
+        tf = sum(m["alg_flops"] for m in per_mode) / (ms_total / 1000.0) / 1e12
+        peak = _fp64_peak_tflops()
+        return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                "traffic": traffic, "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flops x max SM clock",
+                "kernel": "k_mttkrp", "hbm": hbm, "per_mode": per_mode}
+    return {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": gbs / peak_hbm,
+            "traffic": traffic, "peak_kind": kind, "kernel": "k_mttkrp", "per_mode": per_mode}
 
 
 def main():
@@ -213,66 +379,59 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--factor-dtype", default=None)
+    ap.add_argument("--variants", default=None,
+                    help="comma-separated factor dtypes timed after the main one (default f32,bf16 on the "
+                         "default workload; 'none' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-kernel", action="store_true",
                     help="encode once and time only the per-mode MTTKRP launches (profiling runs)")
     args = ap.parse_args()
 
     dist, world, rank, local = _dist_setup()
-    import torch
     import synth
 
     w = synth.WORKLOADS[args.workload]
     spec = w["spec"]
     R, iters = w["R"], w["iters"]
-    fdt = args.factor_dtype or w["factor_dtype"]
+    default_wl = args.workload == DEFAULT_WORKLOAD
+    fdt = args.factor_dtype or (DEFAULT_FACTOR_DTYPE if default_wl else w["factor_dtype"])
+    vlist = args.variants if args.variants is not None else (DEFAULT_VARIANTS if default_wl else "none")
+    variants = [x for x in vlist.split(",") if x and x != "none" and x != fdt]
     N = len(spec.dims)
-    workload_cfg = {"workload": spec.name, "dims": list(spec.dims), "nnz": spec.nnz, "R": R, "iters": iters,
-                    "factor_dtype": fdt, "acc_dtype": "f64" if fdt == "f64" else "f32",
-                    "values": spec.values, "distributions": [list(d) for d in spec.dists]}
+
+    def wcfg(dt):
+        return {"workload": spec.name, "dims": list(spec.dims), "nnz": spec.nnz, "R": R, "iters": iters,
+                "factor_dtype": dt, "acc_dtype": "f64" if dt == "f64" else "f32",
+                "values": spec.values, "distributions": [list(d) for d in spec.dists]}
 
     if args.impl == "reference":
         if rank != 0:
             return
         _, coords, vals = _load_workload(args.workload)
-        sample = min(spec.nnz, CPU_SAMPLE_NNZ)
-        for _ in range(args.warmup):
-            run_cpu_reference(args, w, coords, vals, min(sample, 10_000), iters=0)
-        times, units = [], 0
-        for _ in range(args.steps):
-            thr, dt = run_cpu_reference(args, w, coords, vals, sample)
-            times.append(dt)
-            units += sample * R * N
-        total = sum(times)
-        val = units / total
-        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {**workload_cfg, "sample_nnz": sample, "iters_per_step": 1},
-                "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"first {sample} nonzeros of {spec.name}, 1 CP-ALS iteration "
-                                           f"(all {N} modes) per step, single-threaded C oracle"},
-                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(run_reference(args, w, coords, vals, world)), flush=True)
         return
 
+    import torch
     import paper_2509_00280_gb300 as rl
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t_gen = time.perf_counter()
     _, coords, vals = _load_workload(args.workload)
     t_gen = time.perf_counter() - t_gen
-    torch_fdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[fdt]
-    vals_in = vals.astype(np.float64) if fdt == "f64" else vals
-    d_coords = torch.from_numpy(coords).to(dev)
-    d_vals = torch.from_numpy(vals_in).to(dev)
+    TORCH_DT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
     init = synth.init_factors(spec.dims, R, seed=0)
-    d_init = [torch.from_numpy(f).to(dev).to(torch_fdt).contiguous() for f in init]
-    d_fac = [t.clone() for t in d_init]
     # a dedicated stream: relate_cpals replays a captured CUDA graph per ALS
     # iteration, which needs a non-default stream
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
+
+    def inputs(dt):
+        v_in = vals.astype(np.float64) if dt == "f64" else vals
+        d_init = [torch.from_numpy(f).to(dev).to(TORCH_DT[dt]).contiguous() for f in init]
+        return v_in, torch.from_numpy(coords).to(dev), torch.from_numpy(v_in).to(dev), d_init, \
+            [t.clone() for t in d_init]
+
+    vals_in, d_coords, d_vals, d_init, d_fac = inputs(fdt)
 
     if args.only_kernel:
         h = rl.relate_encode(d_coords, d_vals, spec.dims, factor_dtype=fdt, stream=stream)
@@ -283,19 +442,23 @@ def main():
                 rl.relate_mttkrp(h, n, d_fac, R, out, stream)
         torch.cuda.synchronize()
         h.close()
-        print(json.dumps({"only_kernel": spec.name, "modes": N, "launches_per_mode": max(1, args.steps)}))
+        print(json.dumps({"only_kernel": spec.name, "modes": N, "launches_per_mode": max(1, args.steps),
+                          "factor_dtype": fdt}))
         return
 
-    def step():
-        for a, b in zip(d_fac, d_init):
-            a.copy_(b)
-        h = rl.relate_encode(d_coords, d_vals, spec.dims, factor_dtype=fdt, stream=stream)
-        rl.relate_set_cpals_graph(h, True)
-        res = rl.relate_cpals(h, R, iters, 0.0, d_fac)
-        stats = rl.relate_get_stats(h)
-        h.close()
-        return res, stats
+    def make_step(dt, dc, dv, dfac, dinit):
+        def step():
+            for a, b in zip(dfac, dinit):
+                a.copy_(b)
+            h = rl.relate_encode(dc, dv, spec.dims, factor_dtype=dt, stream=stream)
+            rl.relate_set_cpals_graph(h, True)
+            res = rl.relate_cpals(h, R, iters, 0.0, dfac)
+            stats = rl.relate_get_stats(h)
+            h.close()
+            return res, stats
+        return step
 
+    step = make_step(fdt, d_coords, d_vals, d_fac, d_init)
     for _ in range(args.warmup):
         res, stats = step()
     torch.cuda.synchronize()
@@ -316,42 +479,14 @@ def main():
 
     # --- dominant kernel: per-mode MTTKRP launches timed with events on the stream
     h = rl.relate_encode(d_coords, d_vals, spec.dims, factor_dtype=fdt, stream=stream)
-    stats = rl.relate_get_stats(h)
-    accdt = torch.float64 if fdt == "f64" else torch.float32
-    fb = {"f64": 8, "f32": 4, "bf16": 2}[fdt]
-    ab = 8 if fdt == "f64" else 4
-    vb = 8 if fdt == "f64" else 4
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    per_mode = []
-    reps = 5
-    for n in range(N):
-        out = torch.empty((spec.dims[n], R), dtype=accdt, device=dev)
-        ms = []
-        for r in range(reps + 1):
-            flush.fill_(float(r))  # 256 MB write evicts L2 between launches
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rl.relate_mttkrp(h, n, d_fac, R, out, stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if r:
-                ms.append(e0.elapsed_time(e1))
-        alg = _algorithmic_bytes(stats, n, R, fb, ab, vb)
-        per_mode.append({"mode": n, "ms": statistics.mean(ms), "alg_bytes": alg,
-                         "strategy": rl.relate_get_conflict(h, n, R)})
+    stats, per_mode = _time_kernels(rl, torch, h, stream, d_fac, spec, R, fdt, dev, 5)
     h.close()
-    alg_total = sum(m["alg_bytes"] for m in per_mode)
-    ms_total = sum(m["ms"] for m in per_mode)
-    achieved = (alg_total / N) / (ms_total / N / 1000.0) / 1e9
-    peak, peak_kind = _peaks()
-    traffic = None
-    if NCU_TRAFFIC["sha256"] == _kernel_sha() and NCU_TRAFFIC["workload"] == spec.name:
-        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    roof = _roofline(per_mode, fdt, spec.name)
 
     # --- e2e through the C ABI with host buffers
     pin_c = torch.from_numpy(coords).pin_memory()
     pin_v = torch.from_numpy(vals_in).pin_memory()
-    pin_f = [torch.from_numpy(f).to(torch_fdt).contiguous().pin_memory() for f in init]
+    pin_f = [torch.from_numpy(f).to(TORCH_DT[fdt]).contiguous().pin_memory() for f in init]
     out_f = [torch.empty_like(f).pin_memory() for f in pin_f]
 
     def e2e_step():
@@ -380,29 +515,49 @@ def main():
     e2e_val = units_step * e2e_steps * world / (e2e_ms / 1000.0)
     h2d = coords.nbytes + vals_in.nbytes + sum(f.numel() * f.element_size() for f in pin_f)
     d2h = sum(f.numel() * f.element_size() for f in out_f) + R * 8
+    del pin_c, pin_v, pin_f, out_f
+
+    # --- the other factor precisions of the same workload (same protocol, fewer steps)
+    var_out = {}
+    for vdt in variants:
+        _, vc, vv, vinit, vfac = inputs(vdt)
+        vstep = make_step(vdt, vc, vv, vfac, vinit)
+        vres, _ = vstep()
+        torch.cuda.synchronize()
+        vsteps = max(1, min(args.steps, 3))
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(vsteps):
+            vres, _ = vstep()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        vms = _max_over_ranks(dist, a0.elapsed_time(a1))
+        hv = rl.relate_encode(vc, vv, spec.dims, factor_dtype=vdt, stream=stream)
+        _, vper = _time_kernels(rl, torch, hv, stream, vfac, spec, R, vdt, dev, 3)
+        hv.close()
+        var_out[vdt] = {"value": units_step * vsteps * world / (vms / 1000.0), "unit": UNIT,
+                        "ms_per_step": vms / vsteps, "steps": vsteps, "dtype": "f32",
+                        "final_fit": vres["fit"], "roofline": _roofline(vper, vdt, spec.name)}
+        del vc, vv, vinit, vfac
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fdt == "f64" else "f32",
             "data": "synthetic",
-            "config": {**workload_cfg, "parallelism": f"replicas{world}" if world > 1 else "single",
+            "config": {**wcfg(fdt), "parallelism": f"replicas{world}" if world > 1 else "single",
                        "step": f"encode + {iters} CP-ALS iterations (tol 0), one CUDA graph per iteration",
                        "l2": "inputs larger than L2 (stream %d MB); L2 flushed between kernel timings"
-                             % (spec.nnz * (stats['key_bytes'] + vb) // 2 ** 20),
+                             % (spec.nnz * (stats['key_bytes'] + (8 if fdt == 'f64' else 4)) // 2 ** 20),
                        "final_fit": res["fit"]},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": _launches_per_step(stats, iters, fdt, sum(1 for m in per_mode if m["strategy"] == 2),
                                                R) * args.steps,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_mttkrp", "per_mode": per_mode},
+            "roofline": roof,
             "clocks": clk.summary()}
+    if var_out:
+        line["variants"] = var_out
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = min(spec.nnz, CPU_SAMPLE_NNZ)
-        thr, dt = run_cpu_reference(args, w, coords, vals, sample)
-        line["cpu_baseline"] = {"value": thr, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {sample} nonzeros, 1 CP-ALS iteration (all {N} modes), "
-                                          f"single-threaded C oracle, {dt:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline(w, coords, vals)
     if rank == 0:
         print(f"# generation {t_gen:.1f} s; per-mode MTTKRP ms {[round(m['ms'], 3) for m in per_mode]}",
               file=sys.stderr)

@@ -45,7 +45,9 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so with gcc (portable flags)."""
+    """Compile oracle.c into _build/liboracle.so with gcc (portable flags)
+    (and oracle_omp.c, the CPU baseline's OpenMP MTTKRP)."""
+    build_omp(force)
     os.makedirs(_OUT_DIR, exist_ok=True)
     stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
     if force or stale:
@@ -55,6 +57,63 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+_OMP_SRC = os.path.join(_HERE, "oracle_omp.c")
+_OMP_LIB = os.path.join(_OUT_DIR, "liboracle_omp.so")
+_omp_lib = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile oracle_omp.c (the OpenMP MTTKRP of the CPU baseline) with
+    -O3 -fopenmp, and -mcpu=native on an aarch64 host; FP contraction off, as
+    for the oracle itself."""
+    import platform
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    stale = (not os.path.exists(_OMP_LIB)) or os.path.getmtime(_OMP_LIB) < os.path.getmtime(_OMP_SRC)
+    if force or stale:
+        tmp = _OMP_LIB + f".tmp{os.getpid()}"
+        cpu = ["-mcpu=native"] if platform.machine() in ("aarch64", "arm64") else []
+        cmd = ["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", *cpu,
+               _OMP_SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OMP_LIB)
+    return _OMP_LIB
+
+
+def _load_omp():
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            build_omp()
+            lib = ctypes.CDLL(_OMP_LIB)
+            P = ctypes.c_void_p
+            lib.orc_omp_max_threads.restype, lib.orc_omp_max_threads.argtypes = ctypes.c_int, []
+            lib.orc_mttkrp_omp.restype = ctypes.c_int
+            lib.orc_mttkrp_omp.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P,
+                                           ctypes.c_int, ctypes.c_int64]
+            _omp_lib = lib
+    return _omp_lib
+
+
+def mttkrp_omp(coords: np.ndarray, vals: np.ndarray, dims, mode: int, factors, nthreads: int,
+               priv_limit: int = 4 * 1024 * 1024, out: np.ndarray | None = None) -> np.ndarray:
+    """OpenMP MTTKRP for the CPU baseline's timing (oracle_omp.c): the
+    oracle's per-nonzero arithmetic over nthreads contiguous nonzero chunks;
+    per-thread output copies when I_n x R <= priv_limit, else atomics. Not a
+    correctness reference (its sums are not compensated)."""
+    c = _c(coords, np.uint32)
+    v = _c(vals, np.float64)
+    d = _c(dims, np.uint64)
+    N, nnz = c.shape
+    fs = [_c(f, np.float64) for f in factors]
+    R = fs[0].shape[1]
+    ptrs = (ctypes.c_void_p * N)(*[_p(f) for f in fs])
+    if out is None:
+        out = np.empty((int(d[mode]), R), dtype=np.float64)
+    _check(_load_omp().orc_mttkrp_omp(_p(c), _p(v), _p(d), nnz, N, mode, ptrs, R, _p(out), int(nthreads),
+                                      int(priv_limit)), "mttkrp_omp")
+    return out
 
 
 def _load():

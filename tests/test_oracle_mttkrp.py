@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 
 def _random_sparse(dims, density, rng, int_vals=None):
@@ -153,3 +154,17 @@ def test_compensated_sum_beats_naive_on_long_rows():
     got = oracle.mttkrp(c, v, (1, 3), 0, fs)[0, 0]
     exact = math.fsum(v.tolist())
     assert abs(got - exact) <= 4 * np.spacing(abs(exact)) + 1e-300
+
+
+def test_openmp_baseline_mttkrp_matches_the_oracle():
+    """The CPU baseline's OpenMP MTTKRP (private copies for a short mode,
+    atomics for a long one) equals the compensated oracle up to rounding."""
+    spec = synth.TensorSpec("omp4d", (3000, 800, 90, 24), 200_000, (("zipf", 1.1),) * 3 + (("uniform",),),
+                            values="uniform", value_dtype="f64", seed=12)
+    c, v = synth.make_tensor(spec)
+    fs = synth.init_factors(spec.dims, 24, seed=1)
+    for n in range(4):
+        ref = oracle.mttkrp(c, v, spec.dims, n, fs)
+        for limit in (0, 1 << 30):  # atomics / per-thread copies
+            got = oracle.mttkrp_omp(c, v, spec.dims, n, fs, 4, priv_limit=limit)
+            assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref), (n, limit)
