@@ -385,6 +385,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-kernel", action="store_true",
                     help="encode once and time only the per-mode MTTKRP launches (profiling runs)")
+    ap.add_argument("--plan-depth", type=int, default=None,
+                    help="with --only-kernel: fiber-factoring depth of every mode (relate_set_mode_plan)")
+    ap.add_argument("--col-passes", type=int, default=0,
+                    help="with --only-kernel: column passes of every mode (relate_set_mode_plan)")
     args = ap.parse_args()
 
     dist, world, rank, local = _dist_setup()
@@ -426,7 +430,9 @@ def main():
     torch.cuda.set_stream(stream)
 
     def inputs(dt):
-        v_in = vals.astype(np.float64) if dt == "f64" else vals
+        # the values keep their stored dtype (FP32 values are exact in the FP64
+        # arithmetic of FP64 factors)
+        v_in = vals
         d_init = [torch.from_numpy(f).to(dev).to(TORCH_DT[dt]).contiguous() for f in init]
         return v_in, torch.from_numpy(coords).to(dev), torch.from_numpy(v_in).to(dev), d_init, \
             [t.clone() for t in d_init]
@@ -435,15 +441,27 @@ def main():
 
     if args.only_kernel:
         h = rl.relate_encode(d_coords, d_vals, spec.dims, factor_dtype=fdt, stream=stream)
+        if args.plan_depth is not None or args.col_passes:
+            for n in range(N):
+                rl.relate_set_mode_plan(h, n, -1 if args.plan_depth is None else args.plan_depth, None,
+                                        args.col_passes)
         accdt = torch.float64 if fdt == "f64" else torch.float32
+        ms = []
         for n in range(N):
             out = torch.empty((spec.dims[n], R), dtype=accdt, device=dev)
+            t = []
             for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
                 rl.relate_mttkrp(h, n, d_fac, R, out, stream)
-        torch.cuda.synchronize()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t.append(e0.elapsed_time(e1))
+            ms.append(round(min(t), 3))
+        plans = [rl.relate_get_mode_plan(h, n, R) for n in range(N)]
         h.close()
         print(json.dumps({"only_kernel": spec.name, "modes": N, "launches_per_mode": max(1, args.steps),
-                          "factor_dtype": fdt}))
+                          "factor_dtype": fdt, "ms_per_mode_min": ms, "plans": plans}))
         return
 
     def make_step(dt, dc, dv, dfac, dinit):

@@ -72,7 +72,7 @@ typedef enum { RELATE_F64 = 0, RELATE_F32 = 1, RELATE_BF16 = 2 } relate_dtype_t;
  *               per block (only when it fits; otherwise SEGMENTED runs).
  *  AUTO       - chosen per mode from the encode-time statistics:
  *               PRIVATIZED if I_n x R x acc bytes <= 32 KB (but SEGMENTED when
- *               the mode has <= 31 rows, I_n x R x acc bytes <= 8 KB, its
+ *               the mode has <= 31 rows, I_n x R x acc bytes <= 16 KB, its
  *               hottest row >= 2^15 nonzeros, N <= 5 and 16-byte rows: every
  *               row then sits in the per-block copies), else SEGMENTED if
  *               nnz / distinct(i_n) >= 8 or the mean run of equal i_n >= 8,
@@ -157,6 +157,33 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
 int relate_mttkrp(relate_handle_t h, int mode, void *const *factors, int R, void *out,
                   void *stream);
 
+/* One MTTKRP of a batch: mode `mode` of the tensor encoded in `h`, with the
+ * handle's N factors (host array of DEVICE pointers, factors[mode] not read),
+ * rank R and output `out` (DEVICE, I_mode x R in the handle's acc dtype,
+ * overwritten). */
+typedef struct {
+    relate_handle_t h;
+    int mode;
+    void *const *factors;
+    int R;
+    void *out;
+} relate_mttkrp_item_t;
+
+/* Several MTTKRPs (Sec. 2.2, Fig. 2) in the fewest kernel launches: items
+ * whose handles share N (2..5), the stored word width and the factor dtype,
+ * and that take the vector path (16-byte aligned factors and output, R x
+ * element size a multiple of 16 bytes, partition size a multiple of 4), run
+ * as ONE persistent launch per group of up to 24 items: the items' tiles are
+ * numbered one after the other and a resident grid walks them, each tile
+ * processed as a SEGMENTED tile (rows merged in registers, vector atomics).
+ * Other items run one launch each. Each item's tile order is built on first
+ * use (before any stream capture, as for relate_mttkrp). Results equal the
+ * items' relate_mttkrp results up to the order of floating-point additions.
+ * Asynchronous on `stream` (capturable once the tile orders exist). Items
+ * must not share an output. The paper has no counterpart: this is the
+ * batching of a service's small requests. Errors: INVALID_ARG, OOM, CUDA. */
+int relate_mttkrp_batch(const relate_mttkrp_item_t *items, int nitems, void *stream);
+
 typedef struct {
     double fit;          /* final fit 1 - ||X - Xhat|| / ||X|| */
     int iters;           /* iterations run */
@@ -189,6 +216,29 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
  * (bit budget, Sec. 3.3.1-3.3.2 interleaving); runs / distinct / maxcount are
  * the fiber statistics that pick the synchronisation per mode (the "minimum
  * fiber reuse" rule of Sec. 4.1.3): fiber reuse = nnz / distinct. */
+/* CP-ALS of n problems in lockstep (the relate_cpals algorithm for each):
+ * per iteration and mode s, ONE relate_mttkrp_batch over mode s of every
+ * problem with more than s modes, then each problem's dense update; one
+ * iteration of all active problems is captured as a CUDA graph and replayed,
+ * and re-captured when a problem stops. The host synchronises once per
+ * iteration and stops a problem on its own rule (it > 1 and |fit - fit_prev|
+ * < tol, or NOT_PD, or TIMEOUT, or `iters`); prev_fit (host, n doubles,
+ * nullable; NaN = none) gives the fit before this call, so that a problem
+ * resumed in a later call may stop at its first iteration. hs: n distinct
+ * handles; R: host, n ranks; factors: host array of n host arrays of the
+ * handle's DEVICE factor pointers (in: initial, out: normalised); lambdas:
+ * host array of n pointers to R doubles (host or device memory); infos:
+ * nullable, n entries (fit_trace, if set, must hold `iters` doubles).
+ * stream: a non-default stream; every handle's work runs on it during the
+ * call. Results equal each problem's relate_cpals results up to the order of
+ * floating-point additions. The paper has no counterpart: this is the
+ * batching of a service's small requests. Errors: INVALID_ARG, OOM, CUDA,
+ * and NOT_PD / TIMEOUT of the first problem that stopped with one (infos
+ * tells which). */
+int relate_cpals_batch(relate_handle_t const *hs, int n, const int *R, int iters, double tol,
+                       void *const *const *factors, double *const *lambdas, const double *prev_fit,
+                       relate_cpals_info_t *infos, void *stream);
+
 typedef struct {
     int nmodes;
     int lp;                 /* l(p) */
@@ -215,6 +265,32 @@ int relate_get_conflict(relate_handle_t h, int mode, int R, relate_conflict_t *o
 
 /* Overrides the per-mode strategy (AUTO restores the rule). */
 int relate_set_conflict(relate_handle_t h, int mode, relate_conflict_t c);
+
+/* Fiber-factoring plan of one mode's SEGMENTED MTTKRP (3 to 5 modes). The
+ * per-nonzero MTTKRP of Sec. 2.2 (Fig. 2) is regrouped by distributivity:
+ * with the other modes in `level` order p1, ..., p(N-1), each 2048-nonzero
+ * tile is sorted by (i_n, i_p1, ..., i_p(depth)) once per handle and mode,
+ * and the nonzeros sharing (i_n, i_p1..i_pl) (a level-l fiber, l <= depth)
+ * are summed before one multiply by A_pl(i_pl, :): a factor row is gathered
+ * and multiplied once per fiber instead of once per nonzero. depth 0 = the
+ * flat loop; -1 = AUTO (N - 2 for FP64 factors, whose MTTKRP is bound by the
+ * FP64 pipe; 0 for FP32 / BF16 factors, bound by gather latency).
+ * level: host, N - 1 entries naming every other
+ * mode once; NULL = AUTO (the other modes by decreasing I_k: the largest
+ * factors, whose rows miss in L2, are gathered once per outer fiber). col_passes:
+ * the records of a tile are walked once per chunk of R / col_passes columns
+ * (0 = AUTO = 1; a value that does not split R into whole 16-byte vectors
+ * runs as 1). Results differ from the flat loop by rounding only (the same
+ * terms, another association). Changing depth or level re-sorts the mode's
+ * tiles on its next MTTKRP. Host call. Errors: INVALID_ARG. The paper's
+ * counterpart is the tuned encoding (Sec. 3.3); this plan is a GPU-side
+ * knob of the same search. */
+int relate_set_mode_plan(relate_handle_t h, int mode, int depth, const int8_t *level, int col_passes);
+
+/* The plan relate_mttkrp uses for `mode` at rank R (AUTO resolved; depth 0
+ * when the mode is not SEGMENTED or N is outside 3..5). level: host, N - 1
+ * entries (nullable); depth, col_passes nullable. Errors: INVALID_ARG. */
+int relate_get_mode_plan(relate_handle_t h, int mode, int R, int *depth, int8_t *level, int *col_passes);
 
 /* Changes the factor / accumulation dtypes used by later calls
  * (F64/F64, F32/F32 or BF16/F32): the precision forms of the factors and of

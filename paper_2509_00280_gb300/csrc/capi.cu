@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -185,6 +186,13 @@ struct relate_handle_s {
     uint32_t *d_hot_rows[kMaxModes] = {};
     void *d_hot_scratch = nullptr;  // per-block copies of hot rows (SEGMENTED MTTKRP)
     uint16_t *d_tperm[kMaxModes] = {};  // per-mode tile order (SEGMENTED MTTKRP), built on first use
+    int tperm_depth[kMaxModes] = {};    // the fiber-factoring depth each tile order was sorted for
+    // per-mode fiber-factoring plan (relate_set_mode_plan): depth -1 = AUTO,
+    // level order valid when level_set, column passes 0 = AUTO
+    int plan_depth[kMaxModes] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int8_t plan_level[kMaxModes][kMaxModes] = {};
+    bool level_set[kMaxModes] = {};
+    int plan_passes[kMaxModes] = {};
     double *d_normX2 = nullptr;
     int *d_err = nullptr;  // device error flags of this handle's kernels
     uint64_t runs_n[kMaxModes] = {}, distinct[kMaxModes] = {}, maxcount[kMaxModes] = {};
@@ -381,17 +389,77 @@ void fill_stream_args(const relate_handle_s *h, int mode, MttkrpArgs &a) {
     a.maxcount = h->maxcount[mode];
 }
 
+// Fiber-factoring plan of a mode (mttkrp_fac.cuh): the SEGMENTED strategy of
+// a 3- to 5-mode tensor sums fibers of equal (i_n, i_{p1}, ..., i_{pl}) for
+// l <= depth before multiplying by A_pl. AUTO: depth N - 2 and the other modes
+// ordered longest first, one column pass: the rows of the longest factors,
+// the ones that miss in L2, are gathered once per outer fiber, and the
+// innermost slot (gathered per nonzero) is the shortest factor, which stays
+// in L1 or L2.
+struct ModePlan {
+    int depth;
+    int8_t level[kMaxModes];
+    int passes;
+};
+
+ModePlan resolve_plan(const relate_handle_s *h, int mode, int R) {
+    ModePlan p{};
+    p.passes = h->plan_passes[mode] > 0 ? h->plan_passes[mode] : 1;
+    if (h->N < 3 || h->N > 5 || resolve_conflict(h, mode, R) != RELATE_CONFLICT_SEGMENTED) {
+        p.depth = 0;
+    } else {
+        // AUTO: FP64 factors are bound by the FP64 pipe, so every repeated
+        // fiber saves work: all N - 2 levels (the 150M-nonzero 4-mode workload:
+        // 10.4 against 11.3 ms per mode at 30M nonzeros). FP32 / BF16 factors
+        // are bound by gather latency, and the flat loop, which issues every
+        // gather of a record up front, is faster (2.5 against 3.1 ms FP32).
+        const int autod = h->factor_dtype == RELATE_F64 ? h->N - 2 : 0;
+        p.depth = h->plan_depth[mode] >= 0 ? h->plan_depth[mode] : autod;
+        if (p.depth > h->N - 2) p.depth = h->N - 2;
+    }
+    if (h->level_set[mode]) {
+        for (int s = 0; s < h->N - 1; s++) p.level[s] = h->plan_level[mode][s];
+    } else {
+        int n = 0;
+        for (int k = 0; k < h->N; k++)
+            if (k != mode) p.level[n++] = (int8_t)k;
+        for (int x = 0; x < n; x++)  // stable order by decreasing I_k
+            for (int y = x + 1; y < n; y++)
+                if (h->dims[p.level[y]] > h->dims[p.level[x]]) {
+                    const int8_t t = p.level[x];
+                    p.level[x] = p.level[y];
+                    p.level[y] = t;
+                }
+    }
+    // the sort key (i_n, slots 1..depth, position in the tile) must fit 128 bits
+    int bits = h->lbits[mode] + 11;
+    for (int s = 0; s < p.depth; s++) bits += h->lbits[p.level[s]];
+    while (p.depth > 0 && bits > 128) bits -= h->lbits[p.level[--p.depth]];
+    return p;
+}
+
+void apply_plan(const ModePlan &p, MttkrpArgs &a) {
+    a.depth = p.depth;
+    for (int s = 0; s < kMaxModes; s++) a.level[s] = p.level[s];
+    a.col_passes = p.passes;
+}
+
 // The tile order of a SEGMENTED mode (N <= 5): built once per handle and
-// mode, on `st`, unless `st` is being captured (then the kernel sorts).
-int ensure_tile_order(relate_handle_s *h, int mode, int R, cudaStream_t st) {
+// mode (sorted for the mode's fiber-factoring plan), on `st`, unless `st` is
+// being captured (then the kernel sorts). force: also for another strategy
+// (the batched MTTKRP reads every mode's tile order).
+int ensure_tile_order(relate_handle_s *h, int mode, int R, cudaStream_t st, bool force = false) {
     if (h->d_tperm[mode] || h->nnz == 0 || h->N > 5) return RELATE_OK;
-    if (resolve_conflict(h, mode, R) != RELATE_CONFLICT_SEGMENTED) return RELATE_OK;
+    if (!force && resolve_conflict(h, mode, R) != RELATE_CONFLICT_SEGMENTED) return RELATE_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(st, &cs);
     if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp: capture status");
     if (cs != cudaStreamCaptureStatusNone) return RELATE_OK;
     MttkrpArgs a{};
     fill_stream_args(h, mode, a);
+    const ModePlan plan = resolve_plan(h, mode, R);
+    apply_plan(plan, a);
+    h->tperm_depth[mode] = plan.depth;
     uint16_t *p = nullptr;
     if ((e = dalloc(&p, tperm_bytes(h->nnz), st)) != cudaSuccess) return cuda_fail(e, "relate_mttkrp: tile order");
     if ((e = launch_tile_order(a, h->KW, h->num_sms, p, st)) != cudaSuccess) {
@@ -402,10 +470,23 @@ int ensure_tile_order(relate_handle_s *h, int mode, int R, cudaStream_t st) {
     return RELATE_OK;
 }
 
+// The launch arguments of one mode's MTTKRP of the handle.
+void fill_run_args(relate_handle_s *h, int mode, void *const *factors, int R, void *out, MttkrpArgs &a);
+
 int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *out, cudaStream_t st) {
     int rc0 = ensure_tile_order(h, mode, R, st);
     if (rc0) return rc0;
     MttkrpArgs a{};
+    fill_run_args(h, mode, factors, R, out, a);
+    const int accb = mttkrp_acc_bytes(h->factor_dtype);
+    cudaError_t e = cudaMemsetAsync(out, 0, h->dims[mode] * (size_t)R * accb, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp memset");
+    e = launch_mttkrp(a, h->KW, h->factor_dtype, h->val_dtype, h->smem_budget, h->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp launch");
+    return RELATE_OK;
+}
+
+void fill_run_args(relate_handle_s *h, int mode, void *const *factors, int R, void *out, MttkrpArgs &a) {
     a.words = h->d_words;
     a.vals = h->d_vals;
     a.nnz = h->nnz;
@@ -430,11 +511,140 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
     }
     a.err = h->d_err;
     a.strategy = resolve_conflict(h, mode, R);
-    const int accb = mttkrp_acc_bytes(h->factor_dtype);
-    cudaError_t e = cudaMemsetAsync(out, 0, h->dims[mode] * (size_t)R * accb, st);
-    if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp memset");
-    e = launch_mttkrp(a, h->KW, h->factor_dtype, h->val_dtype, h->smem_budget, h->num_sms, st);
-    if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp launch");
+    apply_plan(resolve_plan(h, mode, R), a);
+    // a tile order sorted without factoring keeps the flat kernel
+    if (h->tperm_depth[mode] == 0) a.depth = 0;
+    a.vals_f64 = h->val_dtype == RELATE_F64;
+}
+
+// One mode of several handles (items) in the fewest launches: items that the
+// batched kernel takes (its tile order built, vector path, N <= 5) are grouped
+// by (N, key width, factor dtype), up to 24 per launch; the others run alone.
+// Outputs are zeroed first.
+struct BatchItemRef {
+    relate_handle_s *h;
+    int mode;
+    void *const *factors;
+    int R;
+    void *out;
+};
+
+int run_mttkrp_batch(const BatchItemRef *items, int n, cudaStream_t st) {
+    struct Group {
+        int N, KW, fdt;
+        std::vector<MttkrpArgs> args;
+    };
+    std::vector<Group> groups;
+    cudaError_t e;
+    int rc;
+    int num_sms = 0;
+    for (int i = 0; i < n; i++) {
+        relate_handle_s *h = items[i].h;
+        const int mode = items[i].mode, R = items[i].R;
+        if ((rc = ensure_tile_order(h, mode, R, st, true)) != RELATE_OK) return rc;
+        MttkrpArgs a{};
+        fill_run_args(h, mode, items[i].factors, R, items[i].out, a);
+        if (!batch_eligible(a, h->factor_dtype)) {
+            if ((rc = run_mttkrp(h, mode, items[i].factors, R, items[i].out, st)) != RELATE_OK) return rc;
+            continue;
+        }
+        const int accb = mttkrp_acc_bytes(h->factor_dtype);
+        if ((e = cudaMemsetAsync(items[i].out, 0, h->dims[mode] * (size_t)R * accb, st)) != cudaSuccess)
+            return cuda_fail(e, "relate_mttkrp_batch memset");
+        num_sms = h->num_sms;
+        Group *g = nullptr;
+        for (auto &x : groups)
+            if (x.N == h->N && x.KW == h->KW && x.fdt == h->factor_dtype) g = &x;
+        if (!g) {
+            groups.push_back(Group{h->N, h->KW, (int)h->factor_dtype, {}});
+            g = &groups.back();
+        }
+        g->args.push_back(a);
+    }
+    for (const auto &g : groups)
+        for (size_t b = 0; b < g.args.size(); b += kBatchItems) {
+            const int cnt = (int)std::min(g.args.size() - b, (size_t)kBatchItems);
+            if ((e = launch_mttkrp_batch(g.args.data() + b, cnt, g.KW, g.fdt, num_sms, st)) != cudaSuccess)
+                return cuda_fail(e, "relate_mttkrp_batch launch");
+        }
+    return RELATE_OK;
+}
+
+// The steps of one ALS sweep, enqueued on the handle's stream (capturable).
+// V of mode m (the other modes' Grams) runs on aux, forked from `st` once the
+// Grams it reads are final: for mode 0 at the start of the iteration; for
+// the later modes of the FP32/FP64 path right after the previous mode's
+// normalised Gram, so that it overlaps that mode's factor store and this
+// mode's MTTKRP (the BF16 path forms the Gram from the stored factor, so
+// it forks at the start of the mode).
+bool tc_path_of(const relate_handle_s *h, int R) { return h->factor_dtype == RELATE_BF16 && gram_tc_supported(R); }
+
+cudaError_t fork_normal_eq(relate_handle_s *h, int R, int m) {
+    const cudaStream_t st = h->stream;
+    cudaError_t x;
+    if ((x = cudaEventRecord(h->ev_g, st)) != cudaSuccess || (x = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess ||
+        (x = launch_normal_eq(h->d_G, h->N, m, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
+                              h->d_status, h->aux)) != cudaSuccess)
+        return x;
+    return cudaEventRecord(h->ev_v, h->aux);
+}
+
+// Before mode n's MTTKRP.
+int mode_pre(relate_handle_s *h, int R, int n) {
+    cudaError_t e;
+    if ((n == 0 || tc_path_of(h, R)) && (e = fork_normal_eq(h, R, n)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals: normal equations");
+    return RELATE_OK;
+}
+
+// After mode n's MTTKRP (into h->d_M): A_n = M V^{-1}, lambda, the normalised
+// factor and its Gram, the fit's inner products.
+int mode_post(relate_handle_s *h, int R, int n, void *const *factors) {
+    const cudaStream_t st = h->stream;
+    const int N = h->N;
+    const int RR = R * R;
+    const int64_t In = (int64_t)h->dims[n];
+    const bool tc_path = tc_path_of(h, R);
+    cudaError_t e;
+    if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess) return cuda_fail(e, "relate_cpals: mode update");
+    if (tc_path) {
+        // lambda from Ahat's column norms, store the normalised BF16 factor,
+        // then its Gram on the tensor cores (of the stored values)
+        if ((e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess ||
+            (e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
+            (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype, st)) !=
+                cudaSuccess ||
+            (e = gram_checked(factors[n], In, R, RELATE_BF16, h->d_scratch, h->d_G + n * RR, h->d_err, st)) !=
+                cudaSuccess ||
+            (e = launch_inner_from_gram(h->d_V, h->d_G + n * RR, h->d_lambda, R, h->d_inner, st)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals: mode update");
+        return RELATE_OK;
+    }
+    // the row pass with its Gram, then finish, have consumed V^{-1} and V:
+    // the next mode's normal equations may overwrite them
+    if ((e = launch_solve_gram(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_scratch, h->d_G + n * RR,
+                               st)) != cudaSuccess ||
+        (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals: mode update");
+    if (n + 1 < N && (e = fork_normal_eq(h, R, n + 1)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals: normal equations");
+    if ((e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype, st)) !=
+        cudaSuccess)
+        return cuda_fail(e, "relate_cpals: mode update");
+    return RELATE_OK;
+}
+
+// After the last mode: the fit, recorded on the device (d_trace) and copied
+// with the status words to the pinned host words fit / status.
+int iteration_fit(relate_handle_s *h, int R, double *p_fit, int *p_stat, double *d_trace, int *d_counter) {
+    const cudaStream_t st = h->stream;
+    cudaError_t e;
+    if ((e = launch_fit(h->d_G, h->N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess ||
+        (d_trace && (e = launch_record_fit(h->d_fit, h->d_status, d_trace, d_counter, st)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(p_fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p_stat, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p_stat + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals: fit");
     return RELATE_OK;
 }
 
@@ -442,68 +652,13 @@ int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *
 // (capturable): results land in the pinned host words fit / status.
 int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_fit, int *p_stat,
                     double *d_trace = nullptr, int *d_counter = nullptr) {
-    const cudaStream_t st = h->stream;
-    const int N = h->N;
-    const int RR = R * R;
-    cudaError_t e;
-    const bool tc_path = h->factor_dtype == RELATE_BF16 && gram_tc_supported(R);
-    // V of mode m (the other modes' Grams) on aux, forked from `st` once the
-    // Grams it reads are final: for mode 0 at the start of the iteration; for
-    // the later modes of the FP32/FP64 path right after the previous mode's
-    // normalised Gram, so that it overlaps that mode's factor store and this
-    // mode's MTTKRP (the BF16 path forms the Gram from the stored factor, so
-    // it forks at the start of the mode)
-    auto fork_normal_eq = [&](int m) -> cudaError_t {
-        cudaError_t x;
-        if ((x = cudaEventRecord(h->ev_g, st)) != cudaSuccess ||
-            (x = cudaStreamWaitEvent(h->aux, h->ev_g, 0)) != cudaSuccess ||
-            (x = launch_normal_eq(h->d_G, N, m, R, h->d_Vinv, h->d_Vinv32, h->d_V, h->acc_dtype == RELATE_F64,
-                                  h->d_status, h->aux)) != cudaSuccess)
-            return x;
-        return cudaEventRecord(h->ev_v, h->aux);
-    };
-    for (int n = 0; n < N; n++) {
-        const int64_t In = (int64_t)h->dims[n];
-        if ((n == 0 || tc_path) && (e = fork_normal_eq(n)) != cudaSuccess)
-            return cuda_fail(e, "relate_cpals: normal equations");
-        int rc = run_mttkrp(h, n, factors, R, h->d_M, st);
-        if (rc) return rc;
-        if ((e = cudaStreamWaitEvent(st, h->ev_v, 0)) != cudaSuccess)
-            return cuda_fail(e, "relate_cpals: mode update");
-        if (tc_path && (e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess)
-            return cuda_fail(e, "relate_cpals: mode update");
-        if (tc_path) {
-            // lambda from Ahat's column norms, store the normalised BF16
-            // factor, then its Gram on the tensor cores (of the stored values)
-            if ((e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
-                (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
-                                        st)) != cudaSuccess ||
-                (e = gram_checked(factors[n], In, R, RELATE_BF16, h->d_scratch, h->d_G + n * RR, h->d_err, st)) !=
-                    cudaSuccess ||
-                (e = launch_inner_from_gram(h->d_V, h->d_G + n * RR, h->d_lambda, R, h->d_inner, st)) !=
-                    cudaSuccess)
-                return cuda_fail(e, "relate_cpals: mode update");
-        } else {
-            // the row pass with its Gram, then finish, have consumed V^{-1}
-            // and V: the next mode's normal equations may overwrite them
-            if ((e = launch_solve_gram(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_scratch,
-                                       h->d_G + n * RR, st)) != cudaSuccess ||
-                (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess)
-                return cuda_fail(e, "relate_cpals: mode update");
-            if (n + 1 < N && (e = fork_normal_eq(n + 1)) != cudaSuccess)
-                return cuda_fail(e, "relate_cpals: normal equations");
-            if ((e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype,
-                                        st)) != cudaSuccess)
-                return cuda_fail(e, "relate_cpals: mode update");
-        }
+    int rc;
+    for (int n = 0; n < h->N; n++) {
+        if ((rc = mode_pre(h, R, n)) != RELATE_OK || (rc = run_mttkrp(h, n, factors, R, h->d_M, h->stream)) != RELATE_OK ||
+            (rc = mode_post(h, R, n, factors)) != RELATE_OK)
+            return rc;
     }
-    if ((e = launch_fit(h->d_G, N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess ||
-        (d_trace && (e = launch_record_fit(h->d_fit, h->d_status, d_trace, d_counter, st)) != cudaSuccess) ||
-        (e = cudaMemcpyAsync(p_fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(p_stat, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(p_stat + 2, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        return cuda_fail(e, "relate_cpals: fit");
-    return RELATE_OK;
+    return iteration_fit(h, R, p_fit, p_stat, d_trace, d_counter);
 }
 
 }  // namespace
@@ -1003,6 +1158,183 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     return rc;
 }
 
+int relate_mttkrp_batch(const relate_mttkrp_item_t *items, int nitems, void *stream) {
+    g_err[0] = 0;
+    if (nitems < 0 || (nitems > 0 && !items)) return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp_batch: bad item list");
+    std::vector<BatchItemRef> refs;
+    refs.reserve(nitems);
+    for (int i = 0; i < nitems; i++) {
+        const relate_mttkrp_item_t &it = items[i];
+        relate_handle_s *h = it.h;
+        if (!h || it.mode < 0 || it.mode >= h->N || it.R < 1 || it.R > RELATE_MAX_RANK || !it.factors || !it.out)
+            return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp_batch: bad item %d", i);
+        for (int k = 0; k < h->N; k++)
+            if (k != it.mode && !it.factors[k])
+                return fail(RELATE_ERR_INVALID_ARG, "relate_mttkrp_batch: item %d: factors[%d] is NULL", i, k);
+        refs.push_back(BatchItemRef{h, it.mode, it.factors, it.R, it.out});
+    }
+    return run_mttkrp_batch(refs.data(), nitems, (cudaStream_t)stream);
+}
+
+int relate_cpals_batch(relate_handle_t const *hs, int n, const int *R, int iters, double tol,
+                       void *const *const *factors, double *const *lambdas, const double *prev_fit,
+                       relate_cpals_info_t *infos, void *stream) {
+    g_err[0] = 0;
+    if (n < 0 || (n > 0 && (!hs || !R || !factors || !lambdas)) || iters < 0)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_cpals_batch: bad argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0 && !st) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals_batch: needs a non-default stream");
+    for (int p = 0; p < n; p++) {
+        if (!hs[p] || R[p] < 1 || R[p] > RELATE_MAX_RANK || !factors[p] || !lambdas[p])
+            return fail(RELATE_ERR_INVALID_ARG, "relate_cpals_batch: bad problem %d", p);
+        for (int k = 0; k < hs[p]->N; k++)
+            if (!factors[p][k]) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals_batch: problem %d factors[%d] NULL", p, k);
+        for (int q = 0; q < p; q++)
+            if (hs[q] == hs[p]) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals_batch: handle %d repeated", p);
+    }
+    // every problem runs on `st` for this call
+    std::vector<cudaStream_t> saved(n);
+    for (int p = 0; p < n; p++) {
+        saved[p] = hs[p]->stream;
+        hs[p]->stream = st;
+    }
+    struct Restore {
+        relate_handle_t const *hs;
+        std::vector<cudaStream_t> &saved;
+        ~Restore() {
+            for (size_t p = 0; p < saved.size(); p++) hs[p]->stream = saved[p];
+        }
+    } restore{hs, saved};
+    int rc;
+    cudaError_t e;
+    int maxN = 0;
+    for (int p = 0; p < n; p++) {
+        relate_handle_s *h = hs[p];
+        if ((rc = ensure_ws(h, R[p])) != RELATE_OK) return rc;
+        for (int m = 0; m < h->N; m++)  // before any capture
+            if ((rc = ensure_tile_order(h, m, R[p], st, true)) != RELATE_OK) return rc;
+        if ((e = cudaMemsetAsync(h->d_status, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "relate_cpals_batch: setup");
+        const int RR = R[p] * R[p];
+        for (int k = 0; k < h->N; k++)
+            if ((e = gram_checked(factors[p][k], (int64_t)h->dims[k], R[p], h->factor_dtype, h->d_scratch,
+                                  h->d_G + k * RR, h->d_err, st)) != cudaSuccess)
+                return cuda_fail(e, "relate_cpals_batch: initial Gram");
+        if (!h->h_pinned && !(h->h_pinned = g_pinned.get()))
+            return fail(RELATE_ERR_OOM, "relate_cpals_batch: pinned host words");
+        maxN = h->N > maxN ? h->N : maxN;
+        if (infos) {
+            infos[p].fit = 0.0;
+            infos[p].iters = 0;
+            infos[p].status = RELATE_OK;
+            infos[p].ridge_retries = 0;
+        }
+    }
+    std::vector<int> active;
+    for (int p = 0; p < n; p++) active.push_back(p);
+    std::vector<double> prev(n, 0.0);
+    std::vector<int> have_prev(n, 0);
+    for (int p = 0; p < n; p++)
+        if (prev_fit && prev_fit[p] == prev_fit[p]) {  // not NaN
+            prev[p] = prev_fit[p];
+            have_prev[p] = 1;
+        }
+    std::vector<int> status(n, RELATE_OK);
+    cudaGraphExec_t gexec = nullptr;
+    bool dirty = true;
+    auto enqueue_iteration = [&]() -> int {
+        for (int s = 0; s < maxN; s++) {
+            std::vector<BatchItemRef> items;
+            for (int p : active) {
+                relate_handle_s *h = hs[p];
+                if (s >= h->N) continue;
+                int r;
+                if ((r = mode_pre(h, R[p], s)) != RELATE_OK) return r;
+                items.push_back(BatchItemRef{h, s, factors[p], R[p], h->d_M});
+            }
+            if (!items.empty() && (rc = run_mttkrp_batch(items.data(), (int)items.size(), st)) != RELATE_OK) return rc;
+            for (int p : active) {
+                relate_handle_s *h = hs[p];
+                if (s >= h->N) continue;
+                int r;
+                if ((r = mode_post(h, R[p], s, factors[p])) != RELATE_OK) return r;
+            }
+        }
+        for (int p : active) {
+            relate_handle_s *h = hs[p];
+            int r;
+            if ((r = iteration_fit(h, R[p], h->h_pinned, reinterpret_cast<int *>(h->h_pinned + 1), nullptr,
+                                   nullptr)) != RELATE_OK)
+                return r;
+        }
+        return RELATE_OK;
+    };
+    for (int it = 1; it <= iters && !active.empty(); it++) {
+        if (dirty) {  // one ALS iteration of the active problems as a CUDA graph
+            if (gexec) cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+            cudaGraph_t g = nullptr;
+            if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(e, "relate_cpals_batch: begin capture");
+            rc = enqueue_iteration();
+            cudaError_t e2 = cudaStreamEndCapture(st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "relate_cpals_batch: end capture");
+            e = cudaGraphInstantiate(&gexec, g, cudaGraphInstantiateFlagUseNodePriority);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "relate_cpals_batch: graph instantiate");
+            dirty = false;
+        }
+        if ((e = cudaGraphLaunch(gexec, st)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            cudaGraphExecDestroy(gexec);
+            return cuda_fail(e, "relate_cpals_batch: iteration");
+        }
+        std::vector<int> still;
+        for (int p : active) {
+            relate_handle_s *h = hs[p];
+            const double fit = h->h_pinned[0];
+            const int *st3 = reinterpret_cast<const int *>(h->h_pinned + 1);
+            bool stop = false;
+            if (infos) {
+                infos[p].fit = fit;
+                infos[p].iters = it;
+                infos[p].ridge_retries = st3[0];
+                if (infos[p].fit_trace) infos[p].fit_trace[it - 1] = fit;
+            }
+            if (st3[2]) {
+                status[p] = RELATE_ERR_TIMEOUT;
+                stop = true;
+            } else if (st3[1]) {
+                status[p] = RELATE_ERR_NOT_PD;
+                stop = true;
+            } else if ((it > 1 || have_prev[p]) && fit - prev[p] < tol && prev[p] - fit < tol) {
+                stop = true;
+            }
+            prev[p] = fit;
+            have_prev[p] = 1;
+            if (stop) dirty = true;
+            else still.push_back(p);
+        }
+        active.swap(still);
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    int first_bad = RELATE_OK;
+    for (int p = 0; p < n; p++) {
+        relate_handle_s *h = hs[p];
+        if (status[p] == RELATE_ERR_TIMEOUT) cudaMemsetAsync(h->d_err, 0, 16, st);
+        if ((e = cudaMemcpyAsync(lambdas[p], h->d_lambda, sizeof(double) * R[p], cudaMemcpyDefault, st)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals_batch: lambda");
+        if (infos) infos[p].status = status[p];
+        if (status[p] != RELATE_OK && first_bad == RELATE_OK) first_bad = status[p];
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "relate_cpals_batch: lambda");
+    if (first_bad != RELATE_OK)
+        return fail(first_bad, "relate_cpals_batch: a problem stopped with %s (see infos)", relate_status_string(first_bad));
+    return RELATE_OK;
+}
+
 int relate_get_stats(relate_handle_t h, relate_stats_t *s) {
     g_err[0] = 0;
     if (!h || !s) return fail(RELATE_ERR_INVALID_ARG, "relate_get_stats: NULL argument");
@@ -1038,6 +1370,47 @@ int relate_set_conflict(relate_handle_t h, int mode, relate_conflict_t c) {
     if (!h || mode < 0 || mode >= h->N || c < RELATE_CONFLICT_AUTO || c > RELATE_CONFLICT_PRIVATIZED)
         return fail(RELATE_ERR_INVALID_ARG, "relate_set_conflict: bad argument");
     h->conflict[mode] = c;
+    return RELATE_OK;
+}
+
+int relate_set_mode_plan(relate_handle_t h, int mode, int depth, const int8_t *level, int col_passes) {
+    g_err[0] = 0;
+    if (!h || mode < 0 || mode >= h->N || depth < -1 || depth > RELATE_MAX_MODES || col_passes < 0 ||
+        col_passes > RELATE_MAX_RANK)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_set_mode_plan: bad argument");
+    if (level) {
+        unsigned seen = 0;
+        for (int s = 0; s < h->N - 1; s++) {
+            const int k = level[s];
+            if (k < 0 || k >= h->N || k == mode || ((seen >> k) & 1u))
+                return fail(RELATE_ERR_INVALID_ARG, "relate_set_mode_plan: level must list the other modes once");
+            seen |= 1u << k;
+        }
+    }
+    const ModePlan before = resolve_plan(h, mode, RELATE_MAX_RANK);
+    h->plan_depth[mode] = depth;
+    h->level_set[mode] = level != nullptr;
+    for (int s = 0; s < kMaxModes; s++) h->plan_level[mode][s] = level && s < h->N - 1 ? level[s] : 0;
+    h->plan_passes[mode] = col_passes;
+    const ModePlan after = resolve_plan(h, mode, RELATE_MAX_RANK);
+    bool same = before.depth == after.depth;
+    for (int s = 0; s < h->N - 1 && same; s++) same = before.level[s] == after.level[s];
+    if (!same && h->d_tperm[mode]) {  // re-sorted on the mode's next MTTKRP
+        cudaFreeAsync(h->d_tperm[mode], h->stream);
+        h->d_tperm[mode] = nullptr;
+    }
+    return RELATE_OK;
+}
+
+int relate_get_mode_plan(relate_handle_t h, int mode, int R, int *depth, int8_t *level, int *col_passes) {
+    g_err[0] = 0;
+    if (!h || mode < 0 || mode >= h->N || R < 1 || R > RELATE_MAX_RANK)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_get_mode_plan: bad argument");
+    const ModePlan p = resolve_plan(h, mode, R);
+    if (depth) *depth = p.depth;
+    if (level)
+        for (int s = 0; s < h->N - 1; s++) level[s] = p.level[s];
+    if (col_passes) *col_passes = p.passes;
     return RELATE_OK;
 }
 

@@ -154,6 +154,13 @@ struct MttkrpArgs {
     int fault_skip_copy;       // test hook: never issue the first tile copy (its wait times out)
     int vals_f64;              // values stored as FP64 (else FP32)
     int *err;                  // device flag: bit 0 = a bounded wait timed out
+    // Fiber factoring of a SEGMENTED mode (0 = off): the record slots 1..N-1
+    // hold the other modes in `level` order, the tile order sorts each tile by
+    // (i_n, slot 1, ..., slot depth), and the kernel sums each fiber of equal
+    // (i_n, slot 1..l) before one multiply by slot l's factor row.
+    int depth;
+    int8_t level[kMaxModes];   // level[s - 1] = the mode in record slot s (s = 1..N-1)
+    int col_passes;            // R split into this many column chunks, one walk of the records each
     // record slot j of a decoded nonzero: slot 0 = the output mode, slots
     // 1..N-1 = the other modes in increasing order (filled by the launcher)
     int rshift[kMaxModes];
@@ -167,8 +174,8 @@ constexpr long long kWaitCycles = 4000000000LL;
 // Upper bound of hot (most populated) rows per mode kept in shared memory.
 constexpr int kHotMax = 256;
 // Global scratch of a handle for the SEGMENTED kernel's per-block copies of
-// the hot rows: 8 KB per block for up to 1024 blocks.
-constexpr size_t kHotBlockBytes = 8192;
+// the hot rows: 16 KB per block for up to 1024 blocks.
+constexpr size_t kHotBlockBytes = 16384;
 constexpr size_t kHotScratchBytes = 1024 * kHotBlockBytes;
 // Hot slots a 16-bit tile-order entry can tag (1 + slot in its top 5 bits).
 constexpr int kHotTagMax = 31;
@@ -192,6 +199,15 @@ cudaError_t launch_hot_table(const uint32_t *counts, uint64_t I, uint32_t *hot_r
 cudaError_t launch_tile_order(const MttkrpArgs &a, int KW, int num_sms, uint16_t *tperm, cudaStream_t st);
 cudaError_t launch_mttkrp(const MttkrpArgs &a, int KW, int factor_dtype, int val_dtype,
                           int smem_budget, int num_sms, cudaStream_t st);
+
+// The batched MTTKRP (one persistent launch over the tiles of up to 24
+// problems sharing N, the key width and the factor dtype, mttkrp_batch.cuh):
+// an item needs its tile order, the vector path (16-byte factor rows and
+// output) and 16-byte aligned tile starts.
+constexpr int kBatchItems = 24;
+bool batch_eligible(const MttkrpArgs &a, int factor_dtype);
+cudaError_t launch_mttkrp_batch(const MttkrpArgs *items, int n, int KW, int factor_dtype, int num_sms,
+                                cudaStream_t st);
 
 // Bytes of shared memory one row of the output accumulator takes.
 int mttkrp_acc_bytes(int factor_dtype);

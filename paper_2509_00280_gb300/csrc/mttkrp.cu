@@ -33,6 +33,43 @@ int max_dynamic_smem(const void *kern) {
 
 int mttkrp_acc_bytes(int factor_dtype) { return factor_dtype == RELATE_F64 ? 8 : 4; }
 
+// Record slots of a launch: slot 0 = the output mode, slots 1..N-1 = the other
+// modes, in a.level order when the mode is fiber-factored (depth >= 1), else
+// in increasing order.
+void fill_slots(MttkrpArgs &a) {
+    a.rshift[0] = a.fields.shift[a.mode];
+    a.rmask[0] = a.fields.mask[a.mode];
+    a.rfac[0] = nullptr;
+    bool use_level = a.depth >= 1;
+    if (use_level) {  // a.level must name every other mode once
+        unsigned seen = 0;
+        for (int s = 0; s < a.N - 1; s++) {
+            const int k = a.level[s];
+            if (k < 0 || k >= a.N || k == a.mode || (seen >> k) & 1u) use_level = false;
+            else seen |= 1u << k;
+        }
+        if (!use_level) a.depth = 0;
+    }
+    int j = 1;
+    for (int s = 0; s < a.N - 1; s++) {
+        int k;
+        if (use_level) {
+            k = a.level[s];
+        } else {
+            k = s < a.mode ? s : s + 1;
+        }
+        a.rshift[j] = a.fields.shift[k];
+        a.rmask[j] = a.fields.mask[k];
+        a.rfac[j] = a.factors[k];
+        j++;
+    }
+    for (; j < kMaxModes; j++) {
+        a.rshift[j] = 0;
+        a.rmask[j] = 0;
+        a.rfac[j] = nullptr;
+    }
+}
+
 cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int val_dtype, int smem_budget,
                           int num_sms, cudaStream_t st) {
     MttkrpArgs a = a_in;
@@ -48,24 +85,30 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
         if (k != a.mode && (reinterpret_cast<uintptr_t>(a.factors[k]) % 16) != 0) vec_ok = false;
 
     a.vals_f64 = val_dtype == RELATE_F64;
-    {
-        int j = 1;
-        a.rshift[0] = a.fields.shift[a.mode];
-        a.rmask[0] = a.fields.mask[a.mode];
-        a.rfac[0] = nullptr;
-        for (int k = 0; k < a.N; k++) {
-            if (k == a.mode) continue;
-            a.rshift[j] = a.fields.shift[k];
-            a.rmask[j] = a.fields.mask[k];
-            a.rfac[j] = a.factors[k];
-            j++;
+    fill_slots(a);
+    const int V = factor_dtype == RELATE_F64 ? 2 : 4;  // elements per lane load
+    if (a.col_passes < 1 || a.R % a.col_passes != 0 || (a.R / a.col_passes) % V != 0) a.col_passes = 1;
+    if (a.strategy == RELATE_CONFLICT_SEGMENTED && a.tperm && vec_ok && a.depth >= 1 && a.N >= 3 && a.N <= 5 &&
+        a.S % 4 == 0 && a.R % V == 0) {
+        // the fiber-factored kernel (mttkrp_fac.cuh): per-block copies of the
+        // hot rows as for the SEGMENTED kernel
+        int hot = 0;
+        if (a.hot_rows && a.In < (1ull << 31) && a.maxcount >= kSegHotMinCount && a.hot_scratch) {
+            hot = (int)(kHotBlockBytes / ((size_t)a.R * accb));
+            if (hot > mk::kTagMax) hot = mk::kTagMax;
+            if (hot > kHotMax) hot = kHotMax;
+            if ((uint64_t)hot > a.In) hot = (int)a.In;
         }
-        for (; j < kMaxModes; j++) {
-            a.rshift[j] = 0;
-            a.rmask[j] = 0;
-            a.rfac[j] = nullptr;
+        a.hot_n = hot;
+        const int64_t tiles = a.P * ((a.S + mk::kTile - 1) / mk::kTile);
+        switch (factor_dtype) {
+        case RELATE_F64: return mttkrp_fac_f64(a, KW, tiles, num_sms, st);
+        case RELATE_F32: return mttkrp_fac_f32(a, KW, tiles, num_sms, st);
+        default: return mttkrp_fac_bf16(a, KW, tiles, num_sms, st);
         }
     }
+    a.depth = 0;
+    fill_slots(a);
     const size_t tile = mk::tile_bytes_for(a.N, KW, factor_dtype, vec_ok, a.vals_f64 ? 8 : 4);
     size_t acc_bytes = 0;
     if (a.strategy == RELATE_CONFLICT_PRIVATIZED && (size_t)a.In * a.R * accb + 16 + tile > (size_t)smem_budget)
@@ -99,7 +142,10 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
         a.hot_n = hot;
         acc_bytes = a.strategy == RELATE_CONFLICT_ATOMIC ? (size_t)hot * a.R * accb : 0;
     }
-    const size_t smem = acc_bytes + 16 + tile;
+    // the compile-time SEGMENTED kernel (tile order present, vector path, N <= 5) needs less shared memory
+    const bool seg_kernel = a.strategy == RELATE_CONFLICT_SEGMENTED && a.tperm && vec_ok && a.N >= 2 && a.N <= 5;
+    const size_t smem = acc_bytes + 16 +
+                        (seg_kernel ? mk::tile_bytes_for(a.N, KW, factor_dtype, vec_ok, a.vals_f64 ? 8 : 4, true) : tile);
     int per_sm = (int)((227 * 1024) / (smem + 1024));
     if (per_sm > 3) per_sm = 3;
     if (per_sm < 1) per_sm = 1;
@@ -129,6 +175,19 @@ cudaError_t launch_tile_order(const MttkrpArgs &a_in, int KW, int num_sms, uint1
     if (a.nnz == 0 || a.P == 0) return cudaSuccess;
     a.hot_n = tile_order_hot_rows(a);
     const int64_t tiles = a.P * ((a.S + mk::kTile - 1) / mk::kTile);
+    if (a.depth >= 1) {  // fiber-factored mode: tiles sorted by (i_n, slots 1..depth)
+        fill_slots(a);
+    }
+    if (a.depth >= 1) {
+        int64_t g = (int64_t)num_sms * 4;
+        if (g > tiles) g = tiles;
+        switch (KW) {
+        case 1: mk::k_tile_order_lex<1><<<(unsigned)g, kThreads, 0, st>>>(a, tperm); break;
+        case 2: mk::k_tile_order_lex<2><<<(unsigned)g, kThreads, 0, st>>>(a, tperm); break;
+        default: mk::k_tile_order_lex<4><<<(unsigned)g, kThreads, 0, st>>>(a, tperm); break;
+        }
+        return cudaGetLastError();
+    }
     int64_t grid = (int64_t)num_sms * 4;
     if (grid > tiles) grid = tiles;
     switch (KW) {
@@ -137,6 +196,67 @@ cudaError_t launch_tile_order(const MttkrpArgs &a_in, int KW, int num_sms, uint1
     default: mk::k_tile_order<4><<<(unsigned)grid, kThreads, 0, st>>>(a, tperm); break;
     }
     return cudaGetLastError();
+}
+
+}  // namespace relate
+
+namespace relate {
+
+bool batch_eligible(const MttkrpArgs &a, int factor_dtype) {
+    const int accb = mttkrp_acc_bytes(factor_dtype);
+    const int fb = factor_dtype == RELATE_F64 ? 8 : factor_dtype == RELATE_F32 ? 4 : 2;
+    if (a.N < 2 || a.N > 5 || !a.tperm || a.S % 4 != 0 || a.nnz == 0 || a.P == 0) return false;
+    if ((a.R * fb) % 16 != 0 || (a.R * accb) % 16 != 0 || (reinterpret_cast<uintptr_t>(a.out) % 16) != 0) return false;
+    for (int k = 0; k < a.N; k++)
+        if (k != a.mode && (reinterpret_cast<uintptr_t>(a.factors[k]) % 16) != 0) return false;
+    return true;
+}
+
+cudaError_t launch_mttkrp_batch(const MttkrpArgs *items, int n, int KW, int factor_dtype, int num_sms,
+                                cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (n > mk::kBatchMax) return cudaErrorInvalidValue;
+    const int V = factor_dtype == RELATE_F64 ? 2 : 4;
+    mk::BatchParams bp{};
+    bp.n = n;
+    bp.wait_cycles = items[0].wait_cycles > 0 ? items[0].wait_cycles : kWaitCycles;
+    bp.fault_skip_copy = items[0].fault_skip_copy;
+    bp.tile_begin[0] = 0;
+    for (int i = 0; i < n; i++) {
+        MttkrpArgs a = items[i];
+        a.depth = 0;
+        fill_slots(a);  // slot 0 = the output mode, then the other modes in increasing order
+        mk::BatchItem &it = bp.it[i];
+        it.words = a.words;
+        it.vals = a.vals;
+        it.tperm = a.tperm;
+        it.nnz = a.nnz;
+        it.S = a.S;
+        it.P = a.P;
+        it.tiles_per_part = (a.S + mk::kTile - 1) / mk::kTile;
+        it.out = a.out;
+        it.R = a.R;
+        const int nvec = (a.R + V - 1) / V;
+        int G = 1, log2G = 0;
+        while (G < nvec && G < 32) {
+            G <<= 1;
+            log2G++;
+        }
+        it.log2G = log2G;
+        it.vals_f64 = a.vals_f64;
+        it.err = a.err;
+        for (int k = 0; k < kMaxModes; k++) {
+            it.rshift[k] = a.rshift[k];
+            it.rmask[k] = a.rmask[k];
+            it.rfac[k] = a.rfac[k];
+        }
+        bp.tile_begin[i + 1] = bp.tile_begin[i] + a.P * it.tiles_per_part;
+    }
+    switch (factor_dtype) {
+    case RELATE_F64: return mttkrp_batch_f64(bp, items[0].N, KW, num_sms, st);
+    case RELATE_F32: return mttkrp_batch_f32(bp, items[0].N, KW, num_sms, st);
+    default: return mttkrp_batch_bf16(bp, items[0].N, KW, num_sms, st);
+    }
 }
 
 }  // namespace relate

@@ -171,10 +171,12 @@ constexpr int kHotHash = 2 * kHotMax;
 __device__ __forceinline__ uint32_t hot_hash(uint32_t row) { return (row * 2654435761u) >> 23; }  // 9 bits
 
 // Shared-memory bytes of the per-tile area: raw stage (words, values of vb
-// bytes), records, row counters, hot-row hash, mbarrier.
-template <int NT, int KW, typename C> constexpr size_t tile_bytes(int vb) {
+// bytes), records, row counters, hot-row hash, mbarrier. The compile-time
+// SEGMENTED kernel (precomputed tile order, hot rows tagged there) needs no
+// row counters and no hash.
+template <int NT, int KW, typename C, bool SEG = false> constexpr size_t tile_bytes(int vb) {
     return (size_t)kTile * (4 * KW) + (size_t)kTile * vb + (size_t)kTile * RecStride<NT, C>::B +
-           (size_t)kSortBins * 4 + (size_t)kHotHash * 8 + 16;
+           (SEG ? (size_t)0 : (size_t)kSortBins * 4 + (size_t)kHotHash * 8) + 16;
 }
 
 // ---- TMA bulk copy (global -> shared) completing on an mbarrier
@@ -267,7 +269,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
     uint32_t *bins = reinterpret_cast<uint32_t *>(srec + (size_t)kTile * RB);
     uint32_t *hkey = bins + kSortBins;     // hot-row hash: keys (row ids)
     uint32_t *hval = hkey + kHotHash;      // and their slots
-    uint64_t *bar = reinterpret_cast<uint64_t *>(hval + kHotHash);
+    // SEG uses neither: the mbarrier follows the records
+    uint64_t *bar = SEG ? reinterpret_cast<uint64_t *>(srec + (size_t)kTile * RB)
+                        : reinterpret_cast<uint64_t *>(hval + kHotHash);
     __shared__ uint32_t wsum[kThreads / 32];
 
     int vj[VPL];
@@ -736,7 +740,7 @@ cudaError_t launch_one(const MttkrpArgs &a, size_t acc_bytes, int grid, cudaStre
         G <<= 1;
         log2G++;
     }
-    const size_t smem = ((acc_bytes + 15) & ~(size_t)15) + tile_bytes<NT, KW, typename Prec<FT>::C>(a.vals_f64 ? 8 : 4);
+    const size_t smem = ((acc_bytes + 15) & ~(size_t)15) + tile_bytes<NT, KW, typename Prec<FT>::C, SEG>(a.vals_f64 ? 8 : 4);
     auto kern = k_mttkrp<NT, KW, FT, VEC, VPL, SEG>;
     cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
@@ -770,25 +774,40 @@ cudaError_t dispatch_ft(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_byt
 #undef RELATE_MK_KW_S
 }
 
-// Per-tile shared bytes of the instantiation a launch will use.
-template <int KW>
+// Per-tile shared bytes of the instantiation a launch will use (seg: the
+// compile-time SEGMENTED kernel).
+template <int KW, bool SEG>
 inline size_t tile_bytes_kw(int NT, bool f64, int vb) {
     switch (NT) {
-    case 2: return f64 ? tile_bytes<2, KW, double>(vb) : tile_bytes<2, KW, float>(vb);
-    case 3: return f64 ? tile_bytes<3, KW, double>(vb) : tile_bytes<3, KW, float>(vb);
-    case 4: return f64 ? tile_bytes<4, KW, double>(vb) : tile_bytes<4, KW, float>(vb);
-    case 5: return f64 ? tile_bytes<5, KW, double>(vb) : tile_bytes<5, KW, float>(vb);
-    default: return f64 ? tile_bytes<0, KW, double>(vb) : tile_bytes<0, KW, float>(vb);
+    case 2: return f64 ? tile_bytes<2, KW, double, SEG>(vb) : tile_bytes<2, KW, float, SEG>(vb);
+    case 3: return f64 ? tile_bytes<3, KW, double, SEG>(vb) : tile_bytes<3, KW, float, SEG>(vb);
+    case 4: return f64 ? tile_bytes<4, KW, double, SEG>(vb) : tile_bytes<4, KW, float, SEG>(vb);
+    case 5: return f64 ? tile_bytes<5, KW, double, SEG>(vb) : tile_bytes<5, KW, float, SEG>(vb);
+    default: return f64 ? tile_bytes<0, KW, double, SEG>(vb) : tile_bytes<0, KW, float, SEG>(vb);
     }
 }
-inline size_t tile_bytes_for(int N, int KW, int factor_dtype, bool vec_ok, int vb) {
+inline size_t tile_bytes_for(int N, int KW, int factor_dtype, bool vec_ok, int vb, bool seg = false) {
     const bool f64 = factor_dtype == RELATE_F64;
     const int NT = (vec_ok && N >= 2 && N <= 5) ? N : 0;
-    return KW == 1 ? tile_bytes_kw<1>(NT, f64, vb) : KW == 2 ? tile_bytes_kw<2>(NT, f64, vb)
-                                                            : tile_bytes_kw<4>(NT, f64, vb);
+    if (seg && NT)
+        return KW == 1 ? tile_bytes_kw<1, true>(NT, f64, vb) : KW == 2 ? tile_bytes_kw<2, true>(NT, f64, vb)
+                                                                      : tile_bytes_kw<4, true>(NT, f64, vb);
+    return KW == 1 ? tile_bytes_kw<1, false>(NT, f64, vb) : KW == 2 ? tile_bytes_kw<2, false>(NT, f64, vb)
+                                                                    : tile_bytes_kw<4, false>(NT, f64, vb);
 }
 
+#include "mttkrp_fac.cuh"
+#include "mttkrp_batch.cuh"
+
 }  // namespace mk
+
+cudaError_t mttkrp_batch_f64(const mk::BatchParams &bp, int N, int KW, int num_sms, cudaStream_t st);
+cudaError_t mttkrp_batch_f32(const mk::BatchParams &bp, int N, int KW, int num_sms, cudaStream_t st);
+cudaError_t mttkrp_batch_bf16(const mk::BatchParams &bp, int N, int KW, int num_sms, cudaStream_t st);
+
+cudaError_t mttkrp_fac_f64(const MttkrpArgs &a, int KW, int64_t tiles, int num_sms, cudaStream_t st);
+cudaError_t mttkrp_fac_f32(const MttkrpArgs &a, int KW, int64_t tiles, int num_sms, cudaStream_t st);
+cudaError_t mttkrp_fac_bf16(const MttkrpArgs &a, int KW, int64_t tiles, int num_sms, cudaStream_t st);
 
 cudaError_t mttkrp_f64(const MttkrpArgs &a, int KW, bool vec_ok, size_t acc_bytes, int grid, cudaStream_t st);
 

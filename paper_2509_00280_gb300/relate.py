@@ -77,6 +77,10 @@ def lib():
                 "relate_get_conflict": (I, [P, I, I, P]),
                 "relate_set_conflict": (I, [P, I, I]),
                 "relate_set_precision": (I, [P, I, I]),
+                "relate_set_mode_plan": (I, [P, I, I, P, I]),
+                "relate_mttkrp_batch": (I, [P, I, P]),
+                "relate_cpals_batch": (I, [P, I, P, I, D, P, P, P, P, P]),
+                "relate_get_mode_plan": (I, [P, I, I, P, P, P]),
                 "relate_set_stream": (I, [P, P]),
                 "relate_set_cpals_graph": (I, [P, I]),
                 "relate_footprint": (I, [P, I, I64, P, I, P]),
@@ -238,6 +242,54 @@ def relate_cpals(h: Handle, R: int, iters: int, tol: float, factors, lam=None):
             "ridge_retries": info.ridge_retries, "fit_trace": trace[:info.iters].copy()}
 
 
+class MttkrpItem(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("mode", ctypes.c_int), ("factors", ctypes.c_void_p), ("R", ctypes.c_int),
+                ("out", ctypes.c_void_p)]
+
+
+def relate_mttkrp_batch(items, stream=None) -> None:
+    """items: list of (handle, mode, factors, R, out); one persistent launch
+    per group of compatible items (relate_mttkrp_batch)."""
+    keep = []
+    arr = (MttkrpItem * max(len(items), 1))()
+    for i, (h, mode, factors, R, out) in enumerate(items):
+        fp = _ptr_array(factors, h.nmodes)
+        keep.append(fp)
+        arr[i] = MttkrpItem(h.raw.value, int(mode), ctypes.cast(fp, ctypes.c_void_p), int(R), _ptr(out))
+    _check(lib().relate_mttkrp_batch(arr, len(items), _stream(stream)), "relate_mttkrp_batch")
+
+
+def relate_cpals_batch(handles, R, iters: int, tol: float, factors, stream, prev_fit=None):
+    """CP-ALS of several problems in lockstep (relate_cpals_batch). handles: n
+    Handles; R: n ranks; factors: n lists of device tensors (updated in place);
+    stream: a non-default torch stream. Returns (n result dicts as
+    relate_cpals's, status of the call)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * max(n, 1))(*[h.raw.value for h in handles])
+    Rs = (ctypes.c_int * max(n, 1))(*[int(r) for r in R])
+    fps = [_ptr_array(f, h.nmodes) for f, h in zip(factors, handles)]
+    fp_arr = (ctypes.c_void_p * max(n, 1))(*[ctypes.cast(x, ctypes.c_void_p).value for x in fps])
+    lams = [np.zeros(int(r), dtype=np.float64) for r in R]
+    lam_arr = (ctypes.c_void_p * max(n, 1))(*[x.ctypes.data for x in lams])
+    traces = [np.zeros(max(iters, 1), dtype=np.float64) for _ in range(n)]
+    infos = (CpalsInfo * max(n, 1))()
+    for i in range(n):
+        infos[i].fit_trace = traces[i].ctypes.data
+    pf = None
+    if prev_fit is not None:
+        pf = np.ascontiguousarray(prev_fit, dtype=np.float64)
+    rc = lib().relate_cpals_batch(hs, n, Rs, int(iters), float(tol), fp_arr, lam_arr,
+                                  pf.ctypes.data if pf is not None else None, infos, _stream(stream))
+    out = []
+    for i in range(n):
+        it = infos[i].iters
+        out.append({"lam": lams[i], "fit": infos[i].fit, "iters": it, "status": infos[i].status,
+                    "ridge_retries": infos[i].ridge_retries, "fit_trace": traces[i][:it].copy()})
+    if rc not in (0, -6, -7):  # NOT_PD / TIMEOUT are per problem (their status)
+        _check(rc, "relate_cpals_batch")
+    return out, rc
+
+
 def relate_get_stats(h: Handle) -> dict:
     s = Stats()
     _check(lib().relate_get_stats(h.raw, ctypes.byref(s)), "relate_get_stats")
@@ -257,6 +309,23 @@ def relate_get_conflict(h: Handle, mode: int, R: int) -> int:
 
 def relate_set_conflict(h: Handle, mode: int, c: int) -> None:
     _check(lib().relate_set_conflict(h.raw, int(mode), int(c)), "relate_set_conflict")
+
+
+def relate_set_mode_plan(h: Handle, mode: int, depth: int = -1, level=None, col_passes: int = 0) -> None:
+    """Fiber-factoring plan of one mode (depth -1 / level None / col_passes 0 = AUTO)."""
+    buf = None
+    if level is not None:
+        buf = np.ascontiguousarray(level, dtype=np.int8)
+    _check(lib().relate_set_mode_plan(h.raw, int(mode), int(depth), buf.ctypes.data if buf is not None else None,
+                                      int(col_passes)), "relate_set_mode_plan")
+
+
+def relate_get_mode_plan(h: Handle, mode: int, R: int) -> dict:
+    d, p = ctypes.c_int(0), ctypes.c_int(0)
+    lv = np.zeros(MAX_MODES, dtype=np.int8)
+    _check(lib().relate_get_mode_plan(h.raw, int(mode), int(R), ctypes.byref(d), lv.ctypes.data, ctypes.byref(p)),
+           "relate_get_mode_plan")
+    return {"depth": d.value, "level": [int(x) for x in lv[:h.nmodes - 1]], "col_passes": p.value}
 
 
 def relate_set_precision(h: Handle, factor_dtype, acc_dtype=None) -> None:

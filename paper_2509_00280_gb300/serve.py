@@ -22,6 +22,14 @@ arithmetic: every request runs the same encode + CP-ALS path (Sec. 3, Sec.
   iteration (relate_set_cpals_graph), and the library's device memory comes
   from the stream-ordered allocator, so one request's release never waits
   for the other streams.
+* Batch lane (small requests). Requests of at most `small_nnz` nonzeros go
+  to one lane that runs up to `batch_max` of them in lockstep
+  (relate_cpals_batch): per iteration and mode ONE persistent MTTKRP launch
+  over the tiles of all of them, one captured CUDA graph per iteration. The
+  lane works in chunks of `chunk_iters` iterations: between chunks finished
+  requests leave and newly admitted ones join (continuous batching at chunk
+  granularity); each request keeps its own stopping rule (its previous fit is
+  carried across chunks).
 
 Latency = completion - arrival, including the host-to-device copy of the
 tensor, the encoding, CP-ALS and the copy of the factors back to the host.
@@ -201,10 +209,12 @@ def percentile(xs, p: float) -> float:
 
 
 class Server:
-    """Worker threads (one CUDA stream each) over an AdmissionQueue."""
+    """Worker threads (one CUDA stream each) over an AdmissionQueue, and
+    optionally a batch lane for small requests (small_nnz > 0)."""
 
     def __init__(self, workers: int = 8, budget_bytes: int | None = None, device: int = 0,
-                 use_graph: bool = True, max_bypass: int = 8):
+                 use_graph: bool = True, max_bypass: int = 8, small_nnz: int = 0, batch_max: int = 16,
+                 chunk_iters: int = 5, small_budget_frac: float = 0.1, small_tol: float = 1e-4):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -214,13 +224,27 @@ class Server:
         if budget_bytes is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget_bytes = int(0.5 * free)
+        self.small_nnz = int(small_nnz)
+        if self.small_nnz > 0:
+            small_budget = int(small_budget_frac * budget_bytes)
+            self.small_queue = AdmissionQueue(small_budget, max_bypass)
+            budget_bytes -= small_budget
+        else:
+            self.small_queue = None
         self.queue = AdmissionQueue(budget_bytes, max_bypass)
         self.use_graph = use_graph
+        self.batch_max = int(batch_max)
+        self.chunk_iters = int(chunk_iters)
+        self.small_tol = float(small_tol)  # the lane's stopping tolerance (one per lockstep call)
         self._t0 = time.perf_counter()
         self._threads = []
         self._errors = []
         for w in range(workers):
             t = threading.Thread(target=self._worker, name=f"relate-serve-{w}", daemon=True)
+            t.start()
+            self._threads.append(t)
+        if self.small_queue is not None:
+            t = threading.Thread(target=self._batch_lane, name="relate-serve-batch", daemon=True)
             t.start()
             self._threads.append(t)
 
@@ -230,11 +254,18 @@ class Server:
     def submit(self, req: Request) -> Future:
         fut: Future = Future()
         req.arrival = self.now()
-        self.queue.put((req, fut), footprint(req))
+        nbytes = footprint(req)
+        if (self.small_queue is not None and req.nnz <= self.small_nnz and nbytes <= self.small_queue.budget
+                and req.tol == self.small_tol):
+            self.small_queue.put((req, fut), nbytes)
+        else:
+            self.queue.put((req, fut), nbytes)
         return fut
 
     def close(self) -> None:
         self.queue.close()
+        if self.small_queue is not None:
+            self.small_queue.close()
         for t in self._threads:
             t.join()
 
@@ -292,6 +323,92 @@ class Server:
                       req.nmodes, nbytes, req.arrival, t_admit, t_start, self.now(), out["fit_trace"])
 
 
+    def _batch_lane(self) -> None:
+        """Small requests in lockstep, in chunks of chunk_iters iterations;
+        admission between chunks (continuous batching)."""
+        torch = self._torch
+        q = self.small_queue
+        try:
+            torch.cuda.set_device(self.device)
+            stream = torch.cuda.Stream(self.device)
+        except BaseException as e:
+            while True:
+                got = q.take()
+                if got is None:
+                    return
+                (req, fut), nbytes = got
+                fut.set_exception(e)
+                q.release(nbytes)
+        active = []  # dicts: req, fut, nbytes, h, factors, prev, iters, trace, t_admit, t_start
+        closed = False
+        while True:
+            while not closed and len(active) < self.batch_max:
+                got = q.take(timeout=0.0 if active else None)
+                if got is None:
+                    closed = q._closed and len(q) == 0
+                    break
+                (req, fut), nbytes = got
+                t_admit = self.now()
+                try:
+                    with torch.cuda.stream(stream):
+                        tdt = getattr(torch, _TORCH_DTYPES[req.precision])
+                        if req.init is not None:
+                            facs = [torch.from_numpy(np.ascontiguousarray(f)).to(self.device).to(tdt).contiguous()
+                                    for f in req.init]
+                        else:
+                            facs = initial_factors(req.dims, req.R, req.init_seed, self.device, tdt)
+                        h = rl.relate_encode(req.coords, req.vals, req.dims, factor_dtype=req.precision,
+                                             stream=stream)
+                    active.append({"req": req, "fut": fut, "nbytes": nbytes, "h": h, "factors": facs,
+                                   "prev": float("nan"), "iters": 0, "trace": [], "t_admit": t_admit,
+                                   "t_start": t_admit, "status": 0})
+                except BaseException as e:
+                    fut.set_exception(e)
+                    q.release(nbytes)
+            if not active:
+                if closed or (q._closed and len(q) == 0):
+                    return
+                continue
+            chunk = min([self.chunk_iters] + [a["req"].max_iters - a["iters"] for a in active])
+            try:
+                with torch.cuda.stream(stream):
+                    res, _ = rl.relate_cpals_batch([a["h"] for a in active], [a["req"].R for a in active], chunk,
+                                                   self.small_tol, [a["factors"] for a in active], stream,
+                                                   prev_fit=[a["prev"] for a in active])
+            except BaseException as e:
+                for a in active:
+                    a["h"].close()
+                    a["fut"].set_exception(e)
+                    q.release(a["nbytes"])
+                active = []
+                continue
+            still = []
+            for a, r in zip(active, res):
+                a["iters"] += r["iters"]
+                a["trace"].extend(r["fit_trace"].tolist())
+                a["prev"] = r["fit"]
+                a["lam"] = r["lam"]
+                a["status"] = r["status"]
+                done = r["status"] != 0 or r["iters"] < chunk or a["iters"] >= a["req"].max_iters
+                if not done:
+                    still.append(a)
+                    continue
+                req = a["req"]
+                try:
+                    host = [f.float().cpu().numpy() if req.precision == "bf16" else f.cpu().numpy()
+                            for f in a["factors"]] if req.return_factors else None
+                    stream.synchronize()
+                    a["fut"].set_result(Result(req.rid, r["fit"], a["iters"], a["status"], a["lam"], host, req.nnz,
+                                               req.R, req.nmodes, a["nbytes"], req.arrival, a["t_admit"],
+                                               a["t_start"], self.now(), np.array(a["trace"])))
+                except BaseException as e:
+                    a["fut"].set_exception(e)
+                finally:
+                    a["h"].close()
+                    q.release(a["nbytes"])
+            active = still
+
+
 def summarize(results, makespan: float) -> dict:
     lat = [r.latency for r in results]
     work = sum(r.work for r in results)
@@ -303,11 +420,14 @@ def summarize(results, makespan: float) -> dict:
 
 
 def run_mix(requests, arrivals=None, workers: int = 8, budget_bytes: int | None = None,
-            use_graph: bool = True):
+            use_graph: bool = True, small_nnz: int = 0, batch_max: int = 16, chunk_iters: int = 5,
+            small_tol: float = 1e-4):
     """Serves `requests` (Request objects). arrivals: None = closed loop (all
     submitted at t = 0), else the arrival time of each request in seconds.
-    Returns (results in request order, summary dict, queue statistics)."""
-    srv = Server(workers=workers, budget_bytes=budget_bytes, use_graph=use_graph)
+    small_nnz > 0 routes requests of at most that many nonzeros to the batch
+    lane. Returns (results in request order, summary dict, queue statistics)."""
+    srv = Server(workers=workers, budget_bytes=budget_bytes, use_graph=use_graph, small_nnz=small_nnz,
+                 batch_max=batch_max, chunk_iters=chunk_iters, small_tol=small_tol)
     futs = []
     t0 = srv.now()
     try:

@@ -15,7 +15,11 @@ replaces the learned policy with a plain search:
 * every (order, partition size) is evaluated once (reward cache);
 * the search stops when the best speedup has not improved for `patience`
   evaluations, or after `max_evals`;
-* per mode, the conflict strategy with the shortest MTTKRP time is kept.
+* per mode, the conflict strategy with the shortest MTTKRP time is kept;
+* then, for the best encoding, every mode's kernel plan is searched
+  (tune_modes): the conflict strategy, and for the SEGMENTED strategy the
+  fiber-factoring depth, the level order of the other modes and the R-tile
+  width (R / column passes), each timed and the fastest kept.
 
 `sandbox_reward` reproduces the paper's sandbox mode (reward for reproducing
 the ALTO order) and serves as a self-test of the search.
@@ -262,6 +266,92 @@ def gpu_evaluator(coords_dev, vals_dev, dims, R: int, factor_dtype: str, factors
     return evaluate
 
 
+@dataclass
+class ModeConfig:
+    strategy: int            # relate_conflict_t (1 atomic, 2 segmented, 3 privatized)
+    depth: int = 0           # fiber-factoring levels (SEGMENTED, 3..5 modes)
+    level: tuple | None = None  # order of the other modes (None = AUTO)
+    col_passes: int = 1      # R-tile width = R / col_passes
+
+    def as_dict(self) -> dict:
+        return {"strategy": self.strategy, "depth": self.depth,
+                "level": list(self.level) if self.level is not None else None, "col_passes": self.col_passes,
+                "rtile": None}
+
+
+def mode_configs(dims, mode: int, R: int, factor_dtype: str) -> list[ModeConfig]:
+    """The kernel plans tune_modes tries for one mode: ATOMIC; PRIVATIZED when
+    the output fits a block's shared memory; SEGMENTED flat and, for 3 to 5
+    modes, at every fiber-factoring depth with the other modes longest first
+    or shortest first, with the whole row or half of it per pass (R-tile)."""
+    N = len(dims)
+    accb = 8 if factor_dtype == "f64" else 4
+    vec = 2 if factor_dtype == "f64" else 4
+    out = [ModeConfig(1), ModeConfig(2)]
+    if int(dims[mode]) * R * accb <= 32 * 1024:
+        out.append(ModeConfig(3))
+    if 3 <= N <= 5:
+        others = [k for k in range(N) if k != mode]
+        longest = tuple(sorted(others, key=lambda k: (-int(dims[k]), k)))
+        shortest = tuple(sorted(others, key=lambda k: (int(dims[k]), k)))
+        passes = [1] + ([2] if R % 2 == 0 and (R // 2) % vec == 0 else [])
+        for depth in range(1, N - 1):
+            for level in dict.fromkeys((longest, shortest)):
+                for p in passes:
+                    out.append(ModeConfig(2, depth, level, p))
+    return out
+
+
+def apply_config(rl, h, mode: int, cfg: ModeConfig) -> None:
+    rl.relate_set_conflict(h, mode, cfg.strategy)
+    rl.relate_set_mode_plan(h, mode, cfg.depth if cfg.strategy == 2 else 0,
+                            list(cfg.level) if cfg.level is not None else None, cfg.col_passes)
+
+
+def tune_modes(h, dims, R: int, factor_dtype: str, factors, reps: int = 3, verbose: bool = False):
+    """Per mode, times every plan of mode_configs on the encoded tensor (CUDA
+    events, L2 flushed between launches) and keeps the fastest; the handle is
+    left with the chosen plans. Returns [(ModeConfig, seconds, AUTO seconds)]."""
+    import torch
+
+    from . import relate as rl
+
+    dev = factors[0].device
+    acc = torch.float64 if factor_dtype == "f64" else torch.float32
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    chosen = []
+    for n in range(len(dims)):
+        out = torch.empty((int(dims[n]), R), dtype=acc, device=dev)
+
+        def time_mode():
+            ts = []
+            for r in range(reps + 1):
+                flush.fill_(float(r))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rl.relate_mttkrp(h, n, factors, R, out)
+                e1.record()
+                torch.cuda.synchronize()
+                if r:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            return float(np.median(ts))
+
+        rl.relate_set_conflict(h, n, 0)
+        rl.relate_set_mode_plan(h, n, -1, None, 0)
+        t_auto = time_mode()
+        best = (math.inf, None)
+        for cfg in mode_configs(dims, n, R, factor_dtype):
+            apply_config(rl, h, n, cfg)
+            t = time_mode()
+            if verbose:
+                print(f"  mode {n} {cfg.as_dict()}: {t * 1e3:.3f} ms", flush=True)
+            if t < best[0]:
+                best = (t, cfg)
+        apply_config(rl, h, n, best[1])
+        chosen.append((best[1], best[0], t_auto))
+    return chosen
+
+
 def main(argv=None):
     """Tunes one named synthetic workload on cuda:0 and prints a JSON line."""
     import argparse
@@ -293,12 +383,21 @@ def main(argv=None):
     dev = torch.device("cuda:0")
     tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[fdt]
     dc = torch.from_numpy(c).to(dev)
-    dv = torch.from_numpy(v.astype(np.float64) if fdt == "f64" else v).to(dev)
+    dv = torch.from_numpy(v).to(dev)
     fs = [torch.from_numpy(f).to(dev).to(tdt).contiguous() for f in synth.init_factors(spec.dims, R, seed=0)]
     t0 = time.time()
     res = tune(spec.dims, gpu_evaluator(dc, dv, spec.dims, R, fdt, fs), partition_sizes=(4096, 8192, 2048),
                max_evals=args.max_evals, patience=args.patience)
+    # the kernel plan of every mode on the best encoding
+    from . import relate as rl
+    h = rl.relate_encode(dc, dv, spec.dims, bit_order=np.array(res.best.order, dtype=np.int8),
+                         partition_size=res.best.partition_size, factor_dtype=fdt)
+    modes = tune_modes(h, spec.dims, R, fdt, fs)
+    h.close()
     line = {"workload": spec.name, "nnz": spec.nnz, "shuffled": args.shuffle, "R": R, "factor_dtype": fdt,
+            "mode_plans": [dict(c.as_dict(), rtile=R // c.col_passes, ms=t * 1e3, auto_ms=ta * 1e3)
+                           for c, t, ta in modes],
+            "tuned_total_ms": sum(t for _, t, _ in modes) * 1e3, "auto_total_ms": sum(ta for _, _, ta in modes) * 1e3,
             "alto_ms": res.baseline.seconds * 1e3, "best_ms": res.best.seconds * 1e3,
             "speedup_over_alto": res.baseline.seconds / res.best.seconds,
             "best_order": list(res.best.order), "best_partition_size": res.best.partition_size,

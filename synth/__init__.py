@@ -395,10 +395,22 @@ WORKLOADS = {
                         150_000_000, (("zipf", 1.1),) * 3 + (("uniform",),),
                         values="uniform", value_dtype="f32", seed=3),
         R=64, iters=10, factor_dtype="f32"),
+    # the same recipe at 30M nonzeros: small case for profiler captures
+    "zipf4d-5Mx1Mx100Kx24-30M": dict(
+        spec=TensorSpec("zipf4d-5Mx1Mx100Kx24-30M", (5_000_000, 1_000_000, 100_000, 24),
+                        30_000_000, (("zipf", 1.1),) * 3 + (("uniform",),),
+                        values="uniform", value_dtype="f32", seed=3),
+        R=64, iters=10, factor_dtype="f32"),
     # 5-mode hyper-sparse
     "zipf5d-10Mx10Mx1Mx1Kx100-100M": dict(
         spec=TensorSpec("zipf5d-10Mx10Mx1Mx1Kx100-100M", (10_000_000, 10_000_000, 1_000_000, 1000, 100),
                         100_000_000, (("zipf", 1.3),) * 2 + (("uniform",),) * 3,
+                        values="uniform", value_dtype="f32", seed=4),
+        R=16, iters=10, factor_dtype="bf16"),
+    # the 5-mode recipe at 20M nonzeros: small case for profiler captures
+    "zipf5d-10Mx10Mx1Mx1Kx100-20M": dict(
+        spec=TensorSpec("zipf5d-10Mx10Mx1Mx1Kx100-20M", (10_000_000, 10_000_000, 1_000_000, 1000, 100),
+                        20_000_000, (("zipf", 1.3),) * 2 + (("uniform",),) * 3,
                         values="uniform", value_dtype="f32", seed=4),
         R=16, iters=10, factor_dtype="bf16"),
 }

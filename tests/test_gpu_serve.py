@@ -5,7 +5,10 @@
   (same kernels; only the order of floating-point atomic additions varies);
 * a served request matches the CPU oracle's CP-ALS from the same initial
   factors (FP64 within 1e-9, FP32 fit within 1e-3);
-* admission keeps the admitted footprint within a small budget.
+* admission keeps the admitted footprint within a small budget;
+* the batch lane (small requests in lockstep, one persistent MTTKRP launch
+  per mode for all of them) gives each request the same CP model alone, in a
+  mix larger than one batch, and through the worker path.
 """
 import numpy as np
 import pytest
@@ -102,3 +105,33 @@ def test_release_cached_memory_after_the_mix():
     res2, _, _ = serve.run_mix(reqs, workers=2)  # the pool grows again on demand
     for a, b in zip(res, res2):
         assert a.iters == b.iters and abs(a.fit - b.fit) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_batch_lane_alone_and_in_the_mix_agree(prec):
+    reqs = serve.with_precision(_mix(10, iters=7), prec)
+    lane = dict(small_nnz=10**9, batch_max=4, chunk_iters=3, small_tol=0.0)
+    mixed, summ, _ = serve.run_mix(reqs, workers=2, **lane)
+    assert summ["requests"] == 10
+    tol = {"f64": 1e-9, "f32": 1e-4, "bf16": 1e-3}[prec]
+    for r, m in zip(reqs, mixed):
+        alone, _, _ = serve.run_mix([r], workers=1, **lane)
+        a = alone[0]
+        assert a.rid == m.rid and a.iters == m.iters == 7 and a.status == m.status == 0
+        assert abs(a.fit - m.fit) <= tol, (prec, r.rid)
+        if prec == "f64":
+            for x, y in zip(a.factors, m.factors):
+                assert np.max(np.abs(x - y)) <= 1e-7
+
+
+def test_batch_lane_matches_the_worker_path_and_the_oracle():
+    reqs = serve.with_precision(_mix(5, nnz_range=(2e4, 8e4), iters=6), "f64")
+    lane, _, _ = serve.run_mix(reqs, workers=1, small_nnz=10**9, batch_max=8, chunk_iters=4, small_tol=0.0)
+    work, _, _ = serve.run_mix(reqs, workers=3)
+    for r, a, b in zip(reqs, lane, work):
+        assert a.iters == b.iters == 6
+        assert np.max(np.abs(a.fit_trace - b.fit_trace)) <= 1e-9
+        init = [np.asarray(f.cpu().numpy(), dtype=np.float64)
+                for f in serve.initial_factors(r.dims, r.R, r.init_seed, DEV, torch.float32)]
+        ref = oracle.cpals(r.coords, r.vals, r.dims, r.R, 6, 0.0, init)
+        assert np.max(np.abs(a.fit_trace - ref["fit_trace"])) <= 1e-9

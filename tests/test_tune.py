@@ -80,3 +80,23 @@ def test_reward_cache_and_patience():
     res = tune.tune(dims, ev2, max_evals=1000, patience=1000)
     assert res.evaluations <= 60 and len(calls) == len(set(calls))
     assert math.isclose(res.best.seconds, min(t.seconds for t in res.trials))
+
+
+def test_mode_configs_enumerate_the_kernel_plans():
+    from paper_2509_00280_gb300 import tune
+    dims = (5000, 1000, 100, 24)
+    cfgs = tune.mode_configs(dims, 0, 64, "f64")
+    # ATOMIC, SEGMENTED flat, then depth 1..2 x 2 level orders x 2 R-tiles
+    assert [c.strategy for c in cfgs[:2]] == [1, 2]
+    fac = [c for c in cfgs if c.depth > 0]
+    assert len(fac) == 2 * 2 * 2
+    assert {c.level for c in fac} == {(1, 2, 3), (3, 2, 1)}
+    assert {c.col_passes for c in fac} == {1, 2}
+    # a 24-row output fits shared memory: PRIVATIZED is tried
+    assert any(c.strategy == 3 for c in tune.mode_configs(dims, 3, 64, "f32"))
+    # 3-mode tensors: one level; R = 12 in FP32 cannot be halved into whole 4-element vectors
+    cfgs3 = tune.mode_configs((300, 200, 100), 1, 12, "f32")
+    assert {c.depth for c in cfgs3 if c.strategy == 2} == {0, 1}
+    assert all(c.col_passes == 1 for c in cfgs3)
+    # 2-mode and 6-mode tensors have no factored plans
+    assert all(c.depth == 0 for c in tune.mode_configs((300, 200), 0, 16, "f32"))
