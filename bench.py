@@ -383,6 +383,9 @@ def main():
                     help="comma-separated factor dtypes timed after the main one (default f32,bf16 on the "
                          "default workload; 'none' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sharded", action="store_true",
+                    help="with N > 1 GPUs: one tensor sharded over the ranks (contiguous equal-nnz slices of the "
+                         "sorted stream, one NCCL all-reduce of M_n per mode; strong scaling) instead of replicas")
     ap.add_argument("--only-kernel", action="store_true",
                     help="encode once and time only the per-mode MTTKRP launches (profiling runs)")
     ap.add_argument("--plan-depth", type=int, default=None,
@@ -401,6 +404,8 @@ def main():
     fdt = args.factor_dtype or (DEFAULT_FACTOR_DTYPE if default_wl else w["factor_dtype"])
     vlist = args.variants if args.variants is not None else (DEFAULT_VARIANTS if default_wl else "none")
     variants = [x for x in vlist.split(",") if x and x != "none" and x != fdt]
+    if args.sharded and world > 1:
+        variants = []  # the sharded line times the main precision only
     N = len(spec.dims)
 
     def wcfg(dt):
@@ -464,13 +469,20 @@ def main():
                           "factor_dtype": fdt, "ms_per_mode_min": ms, "plans": plans}))
         return
 
+    sharded = args.sharded and world > 1
+
     def make_step(dt, dc, dv, dfac, dinit):
         def step():
             for a, b in zip(dfac, dinit):
                 a.copy_(b)
-            h = rl.relate_encode(dc, dv, spec.dims, factor_dtype=dt, stream=stream)
-            rl.relate_set_cpals_graph(h, True)
-            res = rl.relate_cpals(h, R, iters, 0.0, dfac)
+            if sharded:  # this rank's slice of the sorted stream; M_n summed over the ranks
+                from paper_2509_00280_gb300 import shard
+                h = shard.sharded_encode(dc, dv, spec.dims, rank, world, factor_dtype=dt, stream=stream)
+                res = shard.sharded_cpals(h, R, iters, 0.0, dfac)
+            else:
+                h = rl.relate_encode(dc, dv, spec.dims, factor_dtype=dt, stream=stream)
+                rl.relate_set_cpals_graph(h, True)
+                res = rl.relate_cpals(h, R, iters, 0.0, dfac)
             stats = rl.relate_get_stats(h)
             h.close()
             return res, stats
@@ -493,7 +505,9 @@ def main():
     t_ms = ev0.elapsed_time(ev1)
     t_ms = _max_over_ranks(dist, t_ms)
     units_step = spec.nnz * R * N * iters
-    value = units_step * args.steps * world / (t_ms / 1000.0)
+    # replicas: every rank does the whole job (weak scaling); sharded: the
+    # ranks share one job (strong scaling)
+    value = units_step * args.steps * (1 if sharded else world) / (t_ms / 1000.0)
 
     # --- dominant kernel: per-mode MTTKRP launches timed with events on the stream
     h = rl.relate_encode(d_coords, d_vals, spec.dims, factor_dtype=fdt, stream=stream)
@@ -510,9 +524,15 @@ def main():
     def e2e_step():
         for a, b in zip(d_fac, pin_f):
             a.copy_(b, non_blocking=True)
-        h2 = rl.relate_encode(pin_c.numpy(), pin_v.numpy(), spec.dims, factor_dtype=fdt, stream=stream)
-        rl.relate_set_cpals_graph(h2, True)
-        r2 = rl.relate_cpals(h2, R, iters, 0.0, d_fac)
+        if sharded:
+            from paper_2509_00280_gb300 import shard
+            h2 = shard.sharded_encode(pin_c.numpy(), pin_v.numpy(), spec.dims, rank, world, factor_dtype=fdt,
+                                      stream=stream)
+            r2 = shard.sharded_cpals(h2, R, iters, 0.0, d_fac)
+        else:
+            h2 = rl.relate_encode(pin_c.numpy(), pin_v.numpy(), spec.dims, factor_dtype=fdt, stream=stream)
+            rl.relate_set_cpals_graph(h2, True)
+            r2 = rl.relate_cpals(h2, R, iters, 0.0, d_fac)
         for a, b in zip(out_f, d_fac):
             a.copy_(b, non_blocking=True)
         torch.cuda.synchronize()
@@ -530,7 +550,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = _max_over_ranks(dist, e0.elapsed_time(e1))
-    e2e_val = units_step * e2e_steps * world / (e2e_ms / 1000.0)
+    e2e_val = units_step * e2e_steps * (1 if sharded else world) / (e2e_ms / 1000.0)
     h2d = coords.nbytes + vals_in.nbytes + sum(f.numel() * f.element_size() for f in pin_f)
     d2h = sum(f.numel() * f.element_size() for f in out_f) + R * 8
     del pin_c, pin_v, pin_f, out_f
@@ -560,9 +580,10 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fdt == "f64" else "f32",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f64" if fdt == "f64" else "f32",
             "data": "synthetic",
-            "config": {**wcfg(fdt), "parallelism": f"replicas{world}" if world > 1 else "single",
+            "config": {**wcfg(fdt), "parallelism": (f"nnz-shards{world}" if sharded else f"replicas{world}")
+                       if world > 1 else "single",
                        "step": f"encode + {iters} CP-ALS iterations (tol 0), one CUDA graph per iteration",
                        "l2": "inputs larger than L2 (stream %d MB); L2 flushed between kernel timings"
                              % (spec.nnz * (stats['key_bytes'] + (8 if fdt == 'f64' else 4)) // 2 ** 20),

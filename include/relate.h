@@ -115,6 +115,14 @@ typedef struct {
     /* Shared-memory budget (bytes) per thread block for privatised
      * accumulators; 0 = the device maximum minus what the kernel needs. */
     int smem_budget;
+    /* Nonzero sharding over shard_count processes (e.g. one per GPU):
+     * shard_count > 1 keeps only the shard_rank-th contiguous, equal-nnz slice
+     * of the sorted stream (relate_shard_range), the equal-work partitioning
+     * of linearized formats (Sec. 4.2) across devices. Every process passes the
+     * whole tensor; its handle then holds that slice, with its own partitions
+     * and statistics. 0 or 1 = the whole tensor. */
+    int shard_rank;
+    int shard_count;
 } relate_params_t;
 
 /* Fills *p with the defaults (ALTO order, S = 4096, AUTO conflicts, F32
@@ -253,6 +261,8 @@ typedef struct {
     uint64_t distinct[RELATE_MAX_MODES]; /* distinct values of i_n */
     uint64_t maxcount[RELATE_MAX_MODES]; /* largest fiber-slice population */
     int8_t bit_order[RELATE_MAX_KEY_BITS];
+    int64_t nnz_total;      /* nonzeros of the whole tensor (nnz = this shard's) */
+    int64_t shard_lo;       /* position of this shard in the sorted stream */
 } relate_stats_t;
 
 /* Fills the HOST struct *s from the handle (no device work, no
@@ -341,6 +351,31 @@ int relate_release_cached_memory(void);
  * failing iteration and its fit. Default: disabled. The paper has no
  * counterpart (launch overhead only). Errors: INVALID_ARG. */
 int relate_set_cpals_graph(relate_handle_t h, int enable);
+
+/* The shard of a sorted stream of nnz nonzeros that rank `rank` of `count`
+ * holds: [lo, hi) = [floor(nnz * rank / count), floor(nnz * (rank + 1) /
+ * count)), contiguous and of equal size within one nonzero (Sec. 4.2:
+ * equal-work partitions of the linearized stream). Host only; out-of-range
+ * ranks are clamped. */
+void relate_shard_range(int64_t nnz, int rank, int count, int64_t *lo, int64_t *hi);
+
+/* Sums `count` elements of `dtype` (F64 or F32) at the DEVICE address `buf`
+ * over every shard, in place (an all-reduce), ordered on `stream` (enqueue
+ * it on the stream, e.g. ncclAllReduce, or synchronise before reading).
+ * Returns 0 on success. */
+typedef int (*relate_reduce_fn)(void *buf, int64_t count, relate_dtype_t dtype, void *stream, void *user);
+
+/* Makes relate_cpals a sharded CP-ALS: after each mode's MTTKRP it calls
+ * fn(M, I_n * R, acc dtype, stream, user) to sum the shards' partial MTTKRPs
+ * (Sec. 2.2: M is a sum over nonzeros), and at its start fn(norm, 1, F64,
+ * ...) for ||X||^2; every other step (Grams, normal equations, solve,
+ * normalisation, fit) then runs identically on every shard from the same
+ * replicated factors. Graph replay is off while a hook is set. fn NULL
+ * removes the hook. The hook runs on the calling thread between launches,
+ * never inside a stream callback. Errors: INVALID_ARG. relate_cpals reports
+ * a nonzero hook return as RELATE_ERR_CUDA. The paper has no counterpart (its
+ * MTTKRP is one shared-memory process). */
+int relate_set_reduce_hook(relate_handle_t h, relate_reduce_fn fn, void *user);
 
 /* Decodes the linearized tensor {<v_i, p_i>} ordered by p (Sec. 3.3; the
  * inverse of the bit-level encoding of Sec. 3.3.1-3.3.2) to DEVICE buffers,

@@ -209,6 +209,12 @@ struct relate_handle_s {
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_g = nullptr, ev_v = nullptr;
     int use_graph = 0;           // relate_cpals replays a captured iteration
+    // nonzero sharding: this handle holds slice [shard_lo, shard_lo + nnz) of
+    // the globally sorted stream of `nnz_total` nonzeros; relate_cpals sums
+    // each mode's MTTKRP and ||X||^2 over the shards with reduce_fn
+    int64_t nnz_total = 0, shard_lo = 0;
+    relate_reduce_fn reduce_fn = nullptr;
+    void *reduce_user = nullptr;
     double *h_pinned = nullptr;  // pinned host words: fit, status[2], err
 
     // Device memory comes from the stream-ordered allocator and goes back to
@@ -639,7 +645,8 @@ int mode_post(relate_handle_s *h, int R, int n, void *const *factors) {
 int iteration_fit(relate_handle_s *h, int R, double *p_fit, int *p_stat, double *d_trace, int *d_counter) {
     const cudaStream_t st = h->stream;
     cudaError_t e;
-    if ((e = launch_fit(h->d_G, h->N, R, h->d_lambda, h->d_inner, h->d_normX2, h->d_fit, st)) != cudaSuccess ||
+    if ((e = launch_fit(h->d_G, h->N, R, h->d_lambda, h->d_inner, h->d_normX2 + (h->reduce_fn ? 1 : 0), h->d_fit,
+                        st)) != cudaSuccess ||
         (d_trace && (e = launch_record_fit(h->d_fit, h->d_status, d_trace, d_counter, st)) != cudaSuccess) ||
         (e = cudaMemcpyAsync(p_fit, h->d_fit, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(p_stat, h->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
@@ -654,9 +661,12 @@ int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_f
                     double *d_trace = nullptr, int *d_counter = nullptr) {
     int rc;
     for (int n = 0; n < h->N; n++) {
-        if ((rc = mode_pre(h, R, n)) != RELATE_OK || (rc = run_mttkrp(h, n, factors, R, h->d_M, h->stream)) != RELATE_OK ||
-            (rc = mode_post(h, R, n, factors)) != RELATE_OK)
+        if ((rc = mode_pre(h, R, n)) != RELATE_OK || (rc = run_mttkrp(h, n, factors, R, h->d_M, h->stream)) != RELATE_OK)
             return rc;
+        // sharded: the shards' partial MTTKRPs are summed before the update
+        if (h->reduce_fn && h->reduce_fn(h->d_M, (int64_t)h->dims[n] * R, h->acc_dtype, h->stream, h->reduce_user) != 0)
+            return fail(RELATE_ERR_CUDA, "relate_cpals: the reduce hook failed (mode %d)", n);
+        if ((rc = mode_post(h, R, n, factors)) != RELATE_OK) return rc;
     }
     return iteration_fit(h, R, p_fit, p_stat, d_trace, d_counter);
 }
@@ -771,7 +781,21 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
     h->KW = h->lp <= 32 ? 1 : h->lp <= 64 ? 2 : 4;
     build_runs(h);
     h->S = p->partition_size > 0 ? p->partition_size : 4096;
-    h->P = (nnz + h->S - 1) / h->S;
+    // the shard of the sorted stream this handle keeps (all of it unsharded)
+    int64_t shard_lo = 0, shard_hi = nnz;
+    if (p->shard_count > 1) {
+        if (p->shard_rank < 0 || p->shard_rank >= p->shard_count) {
+            delete h;
+            return fail(RELATE_ERR_INVALID_ARG, "relate_encode: shard_rank %d not in [0, %d)", p->shard_rank,
+                        p->shard_count);
+        }
+        relate_shard_range(nnz, p->shard_rank, p->shard_count, &shard_lo, &shard_hi);
+    }
+    const int64_t ns = shard_hi - shard_lo;  // nonzeros kept
+    h->nnz_total = nnz;
+    h->shard_lo = shard_lo;
+    h->nnz = ns;
+    h->P = (ns + h->S - 1) / h->S;
     h->val_dtype = p->val_dtype;
     h->factor_dtype = p->factor_dtype;
     h->acc_dtype = p->acc_dtype;
@@ -815,8 +839,8 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
         const size_t sort_bytes = radix_sort_temp_bytes(nnz);
         // persistent encoding arrays
         // 64 bytes of tail padding: tile copies round their size up to 16 bytes
-        if ((e = dalloc(&h->d_words, words_bytes(nnz, kb), st)) != cudaSuccess ||
-            (e = dalloc(&h->d_vals, vals_bytes(nnz, vb), st)) != cudaSuccess ||
+        if ((e = dalloc(&h->d_words, words_bytes(ns, kb), st)) != cudaSuccess ||
+            (e = dalloc(&h->d_vals, vals_bytes(ns, vb), st)) != cudaSuccess ||
             (e = dalloc((void **)&h->d_plo, bounds_bytes(h->P, N), st)) != cudaSuccess ||
             (e = dalloc((void **)&h->d_phi, bounds_bytes(h->P, N), st)) != cudaSuccess ||
             (e = dalloc((void **)&h->d_normX2, 64, st)) != cudaSuccess ||
@@ -907,14 +931,15 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
             rc = cuda_fail(e, "relate_encode: key build / sort");
             goto done;
         }
-        void *skeys = in_alt ? keys_alt : keys;
-        uint32_t *sperm = (uint32_t *)(in_alt ? idx_alt : idx);
-        if ((e = dalloc((void **)&h->d_perm, perm_bytes(nnz), st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(h->d_perm, sperm, nnz * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
-            (e = launch_make_words_lut(h->KW, skeys, nnz, word_luts, (const unsigned char *)d_luts + kLutMaxBytes,
+        // the handle keeps the shard [shard_lo, shard_hi) of the sorted stream
+        void *skeys = (unsigned char *)(in_alt ? keys_alt : keys) + (size_t)shard_lo * kb;
+        uint32_t *sperm = (uint32_t *)(in_alt ? idx_alt : idx) + shard_lo;
+        if ((e = dalloc((void **)&h->d_perm, perm_bytes(ns), st)) != cudaSuccess ||
+            (ns && (e = cudaMemcpyAsync(h->d_perm, sperm, ns * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) ||
+            (e = launch_make_words_lut(h->KW, skeys, ns, word_luts, (const unsigned char *)d_luts + kLutMaxBytes,
                                        h->d_words, st)) != cudaSuccess ||
             (vals_join.pending && (e = vals_join.join()) != cudaSuccess) ||
-            (e = launch_gather(v_dev, sperm, nnz, vb, h->d_vals, st)) != cudaSuccess) {
+            (e = launch_gather(v_dev, sperm, ns, vb, h->d_vals, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: words / gather");
             goto done;
         }
@@ -923,7 +948,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
             cp.p[m] = h->d_counts[m];
             cp.len[m] = h->dims[m];
         }
-        if ((e = launch_partition_stats(h->KW, h->d_words, nnz, N, h->fields, h->S, h->d_plo, h->d_phi, d_runs, cp,
+        if ((e = launch_partition_stats(h->KW, h->d_words, ns, N, h->fields, h->S, h->d_plo, h->d_phi, d_runs, cp,
                                         st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: partition statistics");
             goto done;
@@ -933,7 +958,7 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
                 rc = cuda_fail(e, "relate_encode: histogram summary");
                 goto done;
             }
-        if ((e = launch_sum_squares(h->d_vals, nnz, vb, d_part, h->d_normX2, st)) != cudaSuccess) {
+        if ((e = launch_sum_squares(h->d_vals, ns, vb, d_part, h->d_normX2, st)) != cudaSuccess) {
             rc = cuda_fail(e, "relate_encode: norm");
             goto done;
         }
@@ -1010,6 +1035,15 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     const int RR = R * R;
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_status, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "relate_cpals: setup");
+    if (h->reduce_fn) {
+        // sharded: ||X||^2 summed over the shards into d_normX2[1], which the
+        // fit reads
+        if ((e = cudaMemcpyAsync(h->d_normX2 + 1, h->d_normX2, sizeof(double), cudaMemcpyDeviceToDevice, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "relate_cpals: norm");
+        if (h->reduce_fn(h->d_normX2 + 1, 1, RELATE_F64, st, h->reduce_user) != 0)
+            return fail(RELATE_ERR_CUDA, "relate_cpals: the reduce hook failed (norm)");
+    }
     for (int k = 0; k < N; k++)
         if ((e = gram_checked(factors[k], (int64_t)h->dims[k], R, h->factor_dtype, h->d_scratch, h->d_G + k * RR,
                               h->d_err, st)) != cudaSuccess)
@@ -1022,8 +1056,10 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     double *p_fit = h->h_pinned;
     int *p_stat = reinterpret_cast<int *>(h->h_pinned + 1);  // status[0], status[1], err
     cudaGraphExec_t gexec = nullptr;
-    // the legacy default stream cannot be captured: graph mode needs a stream
-    const bool graph = h->use_graph && st != nullptr && iters > 0;
+    // the legacy default stream cannot be captured: graph mode needs a stream;
+    // a reduce hook runs host code between the modes, so sharded runs take
+    // the plain path
+    const bool graph = h->use_graph && st != nullptr && iters > 0 && !h->reduce_fn;
     // graph mode with a fixed iteration count (tol <= 0): the iterations are
     // replayed back to back and the host synchronises once, at the end; each
     // replay records its fit on the device
@@ -1191,6 +1227,8 @@ int relate_cpals_batch(relate_handle_t const *hs, int n, const int *R, int iters
             if (!factors[p][k]) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals_batch: problem %d factors[%d] NULL", p, k);
         for (int q = 0; q < p; q++)
             if (hs[q] == hs[p]) return fail(RELATE_ERR_INVALID_ARG, "relate_cpals_batch: handle %d repeated", p);
+        if (hs[p]->reduce_fn)
+            return fail(RELATE_ERR_UNSUPPORTED, "relate_cpals_batch: problem %d is sharded (use relate_cpals)", p);
     }
     // every problem runs on `st` for this call
     std::vector<cudaStream_t> saved(n);
@@ -1345,6 +1383,8 @@ int relate_get_stats(relate_handle_t h, relate_stats_t *s) {
     s->nnz = h->nnz;
     s->partition_size = h->S;
     s->partitions = h->P;
+    s->nnz_total = h->nnz_total;
+    s->shard_lo = h->shard_lo;
     for (int m = 0; m < h->N; m++) {
         s->dims[m] = h->dims[m];
         s->lbits[m] = h->lbits[m];
@@ -1468,6 +1508,23 @@ int relate_release_cached_memory(void) {
     cudaError_t e = lib_pool(&pool);
     if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
     return e == cudaSuccess ? RELATE_OK : cuda_fail(e, "relate_release_cached_memory");
+}
+
+void relate_shard_range(int64_t nnz, int rank, int count, int64_t *lo, int64_t *hi) {
+    if (count < 1) count = 1;
+    if (rank < 0) rank = 0;
+    if (rank >= count) rank = count - 1;
+    if (nnz < 0) nnz = 0;
+    if (lo) *lo = (int64_t)(((__int128)nnz * rank) / count);
+    if (hi) *hi = (int64_t)(((__int128)nnz * (rank + 1)) / count);
+}
+
+int relate_set_reduce_hook(relate_handle_t h, relate_reduce_fn fn, void *user) {
+    g_err[0] = 0;
+    if (!h) return fail(RELATE_ERR_INVALID_ARG, "relate_set_reduce_hook: NULL handle");
+    h->reduce_fn = fn;
+    h->reduce_user = user;
+    return RELATE_OK;
 }
 
 int relate_set_cpals_graph(relate_handle_t h, int enable) {

@@ -33,7 +33,8 @@ class Params(ctypes.Structure):
     _fields_ = [("bit_order", ctypes.c_void_p), ("bit_order_len", ctypes.c_int),
                 ("partition_size", ctypes.c_int64), ("conflict", ctypes.c_int * MAX_MODES),
                 ("val_dtype", ctypes.c_int), ("factor_dtype", ctypes.c_int), ("acc_dtype", ctypes.c_int),
-                ("coords_on_device", ctypes.c_int), ("stream", ctypes.c_void_p), ("smem_budget", ctypes.c_int)]
+                ("coords_on_device", ctypes.c_int), ("stream", ctypes.c_void_p), ("smem_budget", ctypes.c_int),
+                ("shard_rank", ctypes.c_int), ("shard_count", ctypes.c_int)]
 
 
 class CpalsInfo(ctypes.Structure):
@@ -47,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("dims", ctypes.c_uint64 * MAX_MODES), ("lbits", ctypes.c_int * MAX_MODES),
                 ("field_offset", ctypes.c_int * MAX_MODES), ("runs", ctypes.c_uint64 * MAX_MODES),
                 ("distinct", ctypes.c_uint64 * MAX_MODES), ("maxcount", ctypes.c_uint64 * MAX_MODES),
-                ("bit_order", ctypes.c_int8 * MAX_KEY_BITS)]
+                ("bit_order", ctypes.c_int8 * MAX_KEY_BITS), ("nnz_total", ctypes.c_int64), ("shard_lo", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -79,6 +80,8 @@ def lib():
                 "relate_set_precision": (I, [P, I, I]),
                 "relate_set_mode_plan": (I, [P, I, I, P, I]),
                 "relate_mttkrp_batch": (I, [P, I, P]),
+                "relate_shard_range": (None, [I64, I, I, P, P]),
+                "relate_set_reduce_hook": (I, [P, P, P]),
                 "relate_cpals_batch": (I, [P, I, P, I, D, P, P, P, P, P]),
                 "relate_get_mode_plan": (I, [P, I, I, P, P, P]),
                 "relate_set_stream": (I, [P, P]),
@@ -171,7 +174,7 @@ class Handle:
 
 def relate_encode(coords, vals, dims, *, bit_order=None, partition_size: int = 0, conflict=None,
                   val_dtype=None, factor_dtype="f32", acc_dtype=None, stream=None,
-                  smem_budget: int = 0) -> Handle:
+                  smem_budget: int = 0, shard_rank: int = 0, shard_count: int = 1) -> Handle:
     """coords: (N, nnz) uint32 (torch CUDA tensor or host numpy), vals: (nnz,)
     f32/f64 of the same residency. Returns a Handle."""
     on_dev = _is_device(coords)
@@ -204,6 +207,8 @@ def relate_encode(coords, vals, dims, *, bit_order=None, partition_size: int = 0
     p.coords_on_device = 1 if on_dev else 0
     p.stream = _stream(stream)
     p.smem_budget = int(smem_budget)
+    p.shard_rank = int(shard_rank)
+    p.shard_count = int(shard_count)
     dims_arr = np.ascontiguousarray(dims, dtype=np.uint64)
     out = ctypes.c_void_p(0)
     rc = lib().relate_encode(_ptr(coords), _ptr(vals), dims_arr.ctypes.data, N, nnz, ctypes.byref(p),
@@ -298,7 +303,7 @@ def relate_get_stats(h: Handle) -> dict:
             "partition_size": s.partition_size, "partitions": s.partitions,
             "dims": list(s.dims[:N]), "lbits": list(s.lbits[:N]), "field_offset": list(s.field_offset[:N]),
             "runs": list(s.runs[:N]), "distinct": list(s.distinct[:N]), "maxcount": list(s.maxcount[:N]),
-            "bit_order": list(s.bit_order[:s.lp])}
+            "bit_order": list(s.bit_order[:s.lp]), "nnz_total": s.nnz_total, "shard_lo": s.shard_lo}
 
 
 def relate_get_conflict(h: Handle, mode: int, R: int) -> int:
@@ -336,6 +341,38 @@ def relate_set_precision(h: Handle, factor_dtype, acc_dtype=None) -> None:
 
 def relate_set_stream(h: Handle, stream) -> None:
     _check(lib().relate_set_stream(h.raw, _stream(stream)), "relate_set_stream")
+
+
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                             ctypes.c_void_p)
+
+
+def relate_shard_range(nnz: int, rank: int, count: int) -> tuple[int, int]:
+    lo, hi = ctypes.c_int64(0), ctypes.c_int64(0)
+    lib().relate_shard_range(int(nnz), int(rank), int(count), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def relate_set_reduce_hook(h: Handle, fn) -> None:
+    """fn(buf_ptr, count, dtype, stream_ptr) -> int: the all-reduce of a
+    sharded CP-ALS (None removes it). The ctypes callback is kept on the
+    handle for as long as it is set."""
+    if fn is None:
+        h._reduce_cb = None
+        _check(lib().relate_set_reduce_hook(h.raw, None, None), "relate_set_reduce_hook")
+        return
+
+    def trampoline(buf, count, dtype, stream, user):
+        try:
+            return int(fn(buf, count, dtype, stream) or 0)
+        except Exception:  # reported to the library as a failed reduction
+            import traceback
+            traceback.print_exc()
+            return -1
+
+    cb = REDUCE_FN(trampoline)
+    h._reduce_cb = cb
+    _check(lib().relate_set_reduce_hook(h.raw, ctypes.cast(cb, ctypes.c_void_p), None), "relate_set_reduce_hook")
 
 
 class Footprint(ctypes.Structure):
