@@ -65,18 +65,19 @@ typedef enum { RELATE_F64 = 0, RELATE_F32 = 1, RELATE_BF16 = 2 } relate_dtype_t;
  *               mode's first MTTKRP and kept, 2 bytes per nonzero), so each
  *               run of equal rows is merged in registers and written once per
  *               tile; in a mode whose hottest row has >= 2^15 nonzeros, runs
- *               of its hottest rows go to per-block copies in handle-owned
- *               scratch, added into the output once per block.
+ *               of its hottest rows (up to 31) go to per-block copies in
+ *               handle-owned scratch, added into the output once per block;
+ *               a mode with I_n x R x acc bytes <= 16 KB keeps all its rows
+ *               in the per-block copy.
  *  PRIVATIZED - sorted tiles as SEGMENTED, and the whole output (I_n x R) is
  *               privatised in shared memory per thread block and flushed once
  *               per block (only when it fits; otherwise SEGMENTED runs).
  *  AUTO       - chosen per mode from the encode-time statistics:
  *               PRIVATIZED if I_n x R x acc bytes <= 32 KB (but SEGMENTED when
- *               the mode has <= 31 rows, I_n x R x acc bytes <= 16 KB, its
- *               hottest row >= 2^15 nonzeros, N <= 5 and 16-byte rows: every
- *               row then sits in the per-block copies), else SEGMENTED if
- *               nnz / distinct(i_n) >= 8 or the mean run of equal i_n >= 8,
- *               else ATOMIC. */
+ *               I_n x R x acc bytes <= 16 KB, N <= 5 and the rows are whole
+ *               16-byte vectors: every row then sits in the per-block copy in
+ *               scratch), else SEGMENTED if nnz / distinct(i_n) >= 8 or the
+ *               mean run of equal i_n >= 8, else ATOMIC. */
 typedef enum {
     RELATE_CONFLICT_AUTO = 0,
     RELATE_CONFLICT_ATOMIC = 1,

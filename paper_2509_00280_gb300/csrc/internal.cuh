@@ -149,6 +149,7 @@ struct MttkrpArgs {
     int hot_n;                 // hot rows cached in shared memory by this launch
     uint64_t maxcount;         // nonzeros of the mode's most populated row
     void *hot_scratch;         // SEGMENTED: per-block copies of the hot rows (kHotScratchBytes)
+    int full_copy;             // SEGMENTED: every row of the mode in the per-block copy (hot_n = I_n, slot = row)
     const uint16_t *tperm;     // SEGMENTED: precomputed tile order of the mode (null: sort in the kernel)
     long long wait_cycles;     // limit of a bounded wait, SM clock cycles (0: kWaitCycles)
     int fault_skip_copy;       // test hook: never issue the first tile copy (its wait times out)

@@ -93,7 +93,12 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
         // the fiber-factored kernel (mttkrp_fac.cuh): per-block copies of the
         // hot rows as for the SEGMENTED kernel
         int hot = 0;
-        if (a.hot_rows && a.In < (1ull << 31) && a.maxcount >= kSegHotMinCount && a.hot_scratch) {
+        a.full_copy = 0;
+        if (a.hot_scratch && (size_t)a.In * a.R * accb <= kHotBlockBytes) {
+            // a short mode: all its rows in the block's copy
+            a.full_copy = 1;
+            hot = (int)a.In;
+        } else if (a.hot_rows && a.In < (1ull << 31) && a.maxcount >= kSegHotMinCount && a.hot_scratch) {
             hot = (int)(kHotBlockBytes / ((size_t)a.R * accb));
             if (hot > mk::kTagMax) hot = mk::kTagMax;
             if (hot > kHotMax) hot = kHotMax;
@@ -128,17 +133,23 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
         // whose hottest row has enough nonzeros for its global additions to
         // matter.
         int hot = 0;
-        if (a.hot_rows && a.In < (1ull << 31)) {
+        a.full_copy = 0;
+        const bool seg_k = a.strategy == RELATE_CONFLICT_SEGMENTED && a.hot_scratch && a.tperm && vec_ok && a.N >= 2 &&
+                           a.N <= 5;  // the compile-time SEGMENTED kernel
+        if (seg_k && (size_t)a.In * a.R * accb <= kHotBlockBytes) {
+            // a short mode: all its rows in the block's copy (slot = row)
+            a.full_copy = 1;
+            hot = (int)a.In;
+        } else if (a.hot_rows && a.In < (1ull << 31)) {
             if (a.strategy == RELATE_CONFLICT_ATOMIC)
                 hot = (16 * 1024) / (a.R * accb);
-            else if (a.strategy == RELATE_CONFLICT_SEGMENTED && a.maxcount >= kSegHotMinCount && a.hot_scratch &&
-                     a.tperm && vec_ok && a.N >= 2 && a.N <= 5) {  // the compile-time SEGMENTED kernel
+            else if (seg_k && a.maxcount >= kSegHotMinCount) {
                 hot = (int)(kHotBlockBytes / ((size_t)a.R * accb));
                 if (hot > mk::kTagMax) hot = mk::kTagMax;  // slots a tile-order entry can tag
             }
+            if (hot > kHotMax) hot = kHotMax;
+            if ((uint64_t)hot > a.In) hot = (int)a.In;
         }
-        if (hot > kHotMax) hot = kHotMax;
-        if ((uint64_t)hot > a.In) hot = (int)a.In;
         a.hot_n = hot;
         acc_bytes = a.strategy == RELATE_CONFLICT_ATOMIC ? (size_t)hot * a.R * accb : 0;
     }
@@ -153,8 +164,10 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
-    if (a.strategy == RELATE_CONFLICT_SEGMENTED && a.hot_n && (size_t)grid * kHotBlockBytes > kHotScratchBytes)
+    if (a.strategy == RELATE_CONFLICT_SEGMENTED && a.hot_n && (size_t)grid * kHotBlockBytes > kHotScratchBytes) {
         a.hot_n = 0;  // more blocks than scratch copies (over 1024): no hot copies
+        a.full_copy = 0;
+    }
     switch (factor_dtype) {
     case RELATE_F64: return mttkrp_f64(a, KW, vec_ok, acc_bytes, (int)grid, st);
     case RELATE_F32: return mttkrp_f32(a, KW, vec_ok, acc_bytes, (int)grid, st);

@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(kThreads, FacCfg<NT, FT>::MinBlocks) k_mttkrp_
             rec.val = a.vals_f64 ? (C)reinterpret_cast<const double *>(sv)[j] : (C)reinterpret_cast<const float *>(sv)[j];
 #pragma unroll
             for (int k = 0; k < NI; k++) rec.idx[k] = fld(w, a.rshift[k], a.rmask[k]);
-            if (hbin) rec.idx[0] = 0x80000000u | (hbin - 1u);
+            if (a.full_copy) rec.idx[0] |= 0x80000000u;  // every row has its slot: the row itself
+            else if (hbin) rec.idx[0] = 0x80000000u | (hbin - 1u);
             *reinterpret_cast<R_t *>(srec + (size_t)p * RB) = rec;
         }
         __syncthreads();  // records complete; the raw stage is free
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, FacCfg<NT, FT>::MinBlocks) k_mttkrp_
         __syncthreads();
         for (int i = threadIdx.x; i < tot; i += kThreads) {
             const C v = __ldcg(hrep + i);
-            const uint32_t row = __ldg(a.hot_rows + i / R);
+            const uint32_t row = a.full_copy ? (uint32_t)(i / R) : __ldg(a.hot_rows + i / R);
             if (v != C(0) && row != 0xffffffffu) atomicAdd(out + (int64_t)row * R + i % R, v);
         }
     }
@@ -378,7 +379,10 @@ cudaError_t launch_fac_one(const MttkrpArgs &a_in, int64_t tiles, int num_sms, c
     int64_t grid = (int64_t)num_sms * (occ > 0 ? occ : 1);
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
-    if (a.hot_n && (size_t)grid * kHotBlockBytes > kHotScratchBytes) a.hot_n = 0;  // more blocks than copies
+    if (a.hot_n && (size_t)grid * kHotBlockBytes > kHotScratchBytes) {  // more blocks than copies
+        a.hot_n = 0;
+        a.full_copy = 0;
+    }
     kern<<<(unsigned)grid, kThreads, smem, st>>>(a, log2G);
     return cudaGetLastError();
 }

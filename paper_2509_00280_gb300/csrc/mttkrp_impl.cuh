@@ -468,7 +468,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
 #pragma unroll
             for (int k = 0; k < NI; k++) rec.idx[k] = k < N ? fld(w, a.rshift[k], a.rmask[k]) : 0u;
             if (hot_n) {  // slot 0 becomes the run's destination: 0x80000000|slot for a hot row
-                if (SEG || (sorted && direct)) {
+                if (SEG && a.full_copy) {
+                    rec.idx[0] |= 0x80000000u;  // every row has its slot: the row itself
+                } else if (SEG || (sorted && direct)) {
                     if (hbin) rec.idx[0] = 0x80000000u | (hbin - 1u);
                 } else {
                     const uint32_t hs = hot_slot_of(rec.idx[0]);
@@ -615,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_mttkrp(const MttkrpArgs a, cons
         __syncthreads();
         for (int i = threadIdx.x; i < tot; i += kThreads) {
             const C s = SEG ? __ldcg(hrep + i) : sacc[i];
-            const uint32_t row = __ldg(a.hot_rows + i / R);
+            const uint32_t row = (SEG && a.full_copy) ? (uint32_t)(i / R) : __ldg(a.hot_rows + i / R);
             if (s != C(0) && row != 0xffffffffu) atomicAdd(out + (int64_t)row * R + i % R, s);
         }
     }

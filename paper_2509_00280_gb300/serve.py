@@ -471,9 +471,11 @@ def with_precision(requests, precision: str):
 
 
 def main(argv=None):
-    """Serves the request mix at each precision: closed loop to measure the
-    service rate S, then Poisson arrivals at 0.8 S (rate of the first
-    precision). Prints one JSON line per (precision, loop)."""
+    """Serves the request mix in several forms: the first form closed loop
+    measures the service rate S, then every form serves Poisson arrivals at
+    0.8 S (and, with --closed-all, also closed loop). A form is
+    "precision[:lane]": factor precision, and ":lane" sends requests of at most
+    --small-nnz nonzeros to the batch lane. Prints one JSON line per run."""
     import argparse
     import json
     import os
@@ -487,38 +489,56 @@ def main(argv=None):
     ap.add_argument("--nnz-max", type=float, default=2e7)
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=0.0)
-    ap.add_argument("--precisions", default="f32,f64")
+    ap.add_argument("--forms", default="f32:lane,bf16:lane,f64",
+                    help="comma-separated precision[:lane] forms; the first one calibrates the arrival rate")
+    ap.add_argument("--precisions", default=None, help="(older spelling) comma-separated precisions, no lane")
+    ap.add_argument("--small-nnz", type=int, default=200_000)
+    ap.add_argument("--batch-max", type=int, default=16)
+    ap.add_argument("--chunk-iters", type=int, default=5)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-open-loop", action="store_true")
+    ap.add_argument("--closed-all", action="store_true", help="closed loop for every form, not only the first")
     args = ap.parse_args(argv)
     budget = int(args.budget_gb * 2 ** 30) if args.budget_gb > 0 else None
+    forms = args.forms.split(",") if args.precisions is None else args.precisions.split(",")
     rate = None
     lines = []
-    base = None
+    all_fits = {}
     t = time.time()
     mix = make_requests(args.requests, nnz_range=(1e4, args.nnz_max))
     gen_s = time.time() - t
-    for prec in args.precisions.split(","):
+    print(json.dumps({"generated": len(mix), "nnz_total": sum(r.nnz for r in mix), "generation_s": gen_s}),
+          flush=True)
+    for k, form in enumerate(forms):
+        prec, _, opt = form.partition(":")
+        lane = opt == "lane"
         reqs = with_precision(mix, prec)
-        for loop in ("closed", "open"):
+        loops = ["closed", "open"] if (k == 0 or args.closed_all) else ["open"]
+        for loop in loops:
             if loop == "open" and args.no_open_loop:
                 continue
             arr = None if loop == "closed" else synth.poisson_arrivals(len(reqs), rate, seed=0)
             res, summ, q = run_mix(reqs, arr, workers=args.workers, budget_bytes=budget,
-                                   use_graph=not args.no_graph)
+                                   use_graph=not args.no_graph, small_nnz=args.small_nnz if lane else 0,
+                                   batch_max=args.batch_max, chunk_iters=args.chunk_iters,
+                                   small_tol=reqs[0].tol if reqs else 1e-4)
             if loop == "closed" and rate is None:
                 rate = 0.8 * summ["throughput_req_s"]
-            line = {"serve": prec, "loop": loop, "workers": args.workers, "graph": not args.no_graph,
+            line = {"serve": prec, "lane": lane, "small_nnz": args.small_nnz if lane else 0, "loop": loop,
+                    "workers": args.workers, "graph": not args.no_graph,
                     "arrival_rate_req_s": rate if loop == "open" else None, **summ, **q,
-                    "nnz_total": sum(r.nnz for r in reqs), "generation_s": gen_s}
-            if loop == "closed":
-                if base is None:
-                    base = [r.fit for r in res]
-                else:
-                    line["max_fit_diff_vs_first"] = float(max(abs(a - r.fit) for a, r in zip(base, res)))
+                    "nnz_total": sum(r.nnz for r in reqs), "lane_requests": sum(1 for r in reqs if lane and
+                                                                                r.nnz <= args.small_nnz)}
+            fits = {r.rid: r.fit for r in res}
+            all_fits[(form, loop)] = fits
             print(json.dumps(line), flush=True)
             lines.append(line)
         del reqs
+    # every form's fits against the plain FP64 form's (the acceptance bound is 1e-3)
+    ref = next((v for (f, _), v in all_fits.items() if f.partition(":")[0] == "f64"), None)
+    if ref is not None:
+        diff = {f"{f}/{loop}": float(max(abs(ref[i] - v[i]) for i in v)) for (f, loop), v in all_fits.items()}
+        print(json.dumps({"max_fit_diff_vs_f64": diff}), flush=True)
     return lines
 
 

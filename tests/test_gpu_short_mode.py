@@ -1,9 +1,9 @@
-"""The AUTO rule's short, heavily populated mode (Sec. 4.1.3: the
-synchronisation follows the fiber statistics), against the CPU oracle.
+"""The AUTO rule's short modes (Sec. 4.1.3: the synchronisation follows the
+fiber statistics), against the CPU oracle.
 
 A 4-mode tensor of 1M nonzeros whose 24-row mode puts about 41K nonzeros on
-every row (>= 2^15): AUTO takes SEGMENTED with every row of that mode in the
-per-block copies. Checked for FP64, FP32 and BF16 factors, with 16-byte
+every row: AUTO takes SEGMENTED with every row of that mode in the per-block
+copy (its output is at most 16 KB). Checked for FP64, FP32 and BF16 factors, with 16-byte
 aligned factors (vector path) and with factors one element off 16 bytes
 (scalar path: no per-block copies, every run flushed by global atomics).
 Tolerances as for every MTTKRP test: FP64 1e-12, FP32 1e-5, BF16 1e-5
@@ -65,4 +65,24 @@ def test_short_hot_mode_auto_segmented(short_mode_tensor, fdt, offset):
         ref = oracle.mttkrp(c, v.astype(np.float64), spec.dims, n, fs)
         assert rel_fro(out.cpu().numpy(), ref) <= TOL[fdt], (fdt, offset, n)
     rl.relate_sync_status(h)
+    h.close()
+
+
+def test_hundred_row_mode_keeps_every_row_in_the_block_copy():
+    """A 100-row mode of a 5-mode BF16 tensor (6.4 KB of FP32 output at R = 16,
+    ~10K nonzeros per row): AUTO SEGMENTED with all rows in the per-block
+    copy, within the BF16 tolerance (1e-5 against the rounded factors)."""
+    spec = synth.TensorSpec("short5d", (4000, 3000, 500, 60, 100), 1_000_000, (("zipf", 1.3),) * 2 + (("uniform",),) * 3,
+                            values="uniform", value_dtype="f32", seed=42)
+    c, v = synth.make_tensor(spec)
+    R = 16
+    h = encode_dev(c, v, spec.dims, factor_dtype="bf16")
+    assert rl.relate_get_conflict(h, 4, R) == rl.RELATE_CONFLICT_SEGMENTED
+    fs, dfs = _factors(spec.dims, R, "bf16", 0)
+    for n in (4, 3):
+        out = torch.empty((spec.dims[n], R), dtype=torch.float32, device=DEV)
+        rl.relate_mttkrp(h, n, dfs, R, out)
+        torch.cuda.synchronize()
+        ref = oracle.mttkrp(c, v.astype(np.float64), spec.dims, n, fs)
+        assert rel_fro(out.cpu().numpy(), ref) <= 1e-5, n
     h.close()
