@@ -52,11 +52,11 @@ NUM_SMS = 152
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": "b95f435e32cd5dd9716be6ae0ccdfb7600a6e49460af90a901e7ebb066b690b6",
-               # 20M-nonzero capture (336.9 MB per launch), stream part (8-byte
-               # word, 4-byte value, 2-byte tile-order entry) scaled to 50M
-               # nonzeros: 336.9 MB + 30M x 14 B
-               "bytes_per_launch": 756.9e6, "workload": "zipf3d-200Kx200Kx5K-50M"}
+NCU_TRAFFIC = {"sha256": "b5bd63573afc8791af38b7c0c8b1ac06fe4c6285dfc65b50f93e284c2ed40a9b",
+               # full-size 1-pass capture (dram__bytes_read.sum + dram__bytes_write.sum)
+               # of the 4 per-mode launches of the FP64 factored MTTKRP: 19.94 / 18.51
+               # / 17.36 / 16.21 GB, their mean
+               "bytes_per_launch": 18.0e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
 
 
 def _peaks():
@@ -87,7 +87,7 @@ def _kernel_sha() -> str:
     invalidate the ncu counters)."""
     import re
     h = hashlib.sha256()
-    for name in ("mttkrp_impl.cuh", "mttkrp.cu"):
+    for name in ("mttkrp_impl.cuh", "mttkrp.cu", "mttkrp_fac.cuh"):
         with open(os.path.join(ROOT, "paper_2509_00280_gb300", "csrc", name)) as f:
             src = f.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -366,7 +366,7 @@ def _roofline(per_mode, fdt, workload):
         peak = _fp64_peak_tflops()
         return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                 "traffic": traffic, "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flops x max SM clock",
-                "kernel": "k_mttkrp", "hbm": hbm, "per_mode": per_mode}
+                "kernel": "k_mttkrp_fac", "hbm": hbm, "per_mode": per_mode}
     return {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": gbs / peak_hbm,
             "traffic": traffic, "peak_kind": kind, "kernel": "k_mttkrp", "per_mode": per_mode}
 

@@ -631,10 +631,11 @@ int mode_post(relate_handle_s *h, int R, int n, void *const *factors) {
             return cuda_fail(e, "relate_cpals: mode update");
         return RELATE_OK;
     }
-    // the row pass with its Gram, then finish, have consumed V^{-1} and V:
-    // the next mode's normal equations may overwrite them
-    if ((e = launch_solve_gram(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_scratch, h->d_G + n * RR,
-                               st)) != cudaSuccess ||
+    // the row pass and the Gram of its result (tensor cores), then finish,
+    // have consumed V^{-1} and V: the next mode's normal equations may
+    // overwrite them
+    if ((e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess ||
+        (e = gram_checked(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, h->d_err, st)) != cudaSuccess ||
         (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals: mode update");
     if (n + 1 < N && (e = fork_normal_eq(h, R, n + 1)) != cudaSuccess)
@@ -1282,34 +1283,66 @@ int relate_cpals_batch(relate_handle_t const *hs, int n, const int *R, int iters
             have_prev[p] = 1;
         }
     std::vector<int> status(n, RELATE_OK);
+    // Each problem's dense steps (normal equations, row pass, Gram, fit) run
+    // on a branch stream of its own, forked from `st` after each batched
+    // MTTKRP and joined before the next, so that in the captured graph the
+    // problems' small kernels are independent nodes that run side by side.
+    struct Branches {
+        std::vector<cudaStream_t> s;
+        std::vector<cudaEvent_t> ev;
+        cudaEvent_t fork = nullptr;
+        ~Branches() {
+            for (cudaStream_t x : s) cudaStreamDestroy(x);
+            for (cudaEvent_t x : ev) cudaEventDestroy(x);
+            if (fork) cudaEventDestroy(fork);
+        }
+    } br;
+    if (n > 0 && (e = cudaEventCreateWithFlags(&br.fork, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "relate_cpals_batch: branch streams");
+    for (int p = 0; p < n; p++) {
+        cudaStream_t x = nullptr;
+        cudaEvent_t v = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals_batch: branch streams");
+        br.s.push_back(x);
+        if ((e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "relate_cpals_batch: branch streams");
+        br.ev.push_back(v);
+    }
+    // runs step(p) for every active problem with s < N on its branch, between a fork from and a join into `st`
+    auto on_branches = [&](int s, auto step) -> int {
+        cudaError_t x;
+        if ((x = cudaEventRecord(br.fork, st)) != cudaSuccess) return cuda_fail(x, "relate_cpals_batch: fork");
+        for (int p : active) {
+            relate_handle_s *h = hs[p];
+            if (s >= h->N) continue;
+            h->stream = br.s[p];
+            if ((x = cudaStreamWaitEvent(br.s[p], br.fork, 0)) != cudaSuccess) return cuda_fail(x, "relate_cpals_batch: fork");
+            const int r = step(p);
+            h->stream = st;
+            if (r != RELATE_OK) return r;
+            if ((x = cudaEventRecord(br.ev[p], br.s[p])) != cudaSuccess || (x = cudaStreamWaitEvent(st, br.ev[p], 0)) != cudaSuccess)
+                return cuda_fail(x, "relate_cpals_batch: join");
+        }
+        return RELATE_OK;
+    };
     cudaGraphExec_t gexec = nullptr;
     bool dirty = true;
     auto enqueue_iteration = [&]() -> int {
         for (int s = 0; s < maxN; s++) {
             std::vector<BatchItemRef> items;
-            for (int p : active) {
-                relate_handle_s *h = hs[p];
-                if (s >= h->N) continue;
-                int r;
-                if ((r = mode_pre(h, R[p], s)) != RELATE_OK) return r;
-                items.push_back(BatchItemRef{h, s, factors[p], R[p], h->d_M});
-            }
+            int r = on_branches(s, [&](int p) { return mode_pre(hs[p], R[p], s); });
+            if (r != RELATE_OK) return r;
+            for (int p : active)
+                if (s < hs[p]->N) items.push_back(BatchItemRef{hs[p], s, factors[p], R[p], hs[p]->d_M});
             if (!items.empty() && (rc = run_mttkrp_batch(items.data(), (int)items.size(), st)) != RELATE_OK) return rc;
-            for (int p : active) {
-                relate_handle_s *h = hs[p];
-                if (s >= h->N) continue;
-                int r;
-                if ((r = mode_post(h, R[p], s, factors[p])) != RELATE_OK) return r;
-            }
-        }
-        for (int p : active) {
-            relate_handle_s *h = hs[p];
-            int r;
-            if ((r = iteration_fit(h, R[p], h->h_pinned, reinterpret_cast<int *>(h->h_pinned + 1), nullptr,
-                                   nullptr)) != RELATE_OK)
+            if ((r = on_branches(s, [&](int p) { return mode_post(hs[p], R[p], s, factors[p]); })) != RELATE_OK)
                 return r;
         }
-        return RELATE_OK;
+        return on_branches(0, [&](int p) {
+            relate_handle_s *h = hs[p];
+            return iteration_fit(h, R[p], h->h_pinned, reinterpret_cast<int *>(h->h_pinned + 1), nullptr, nullptr);
+        });
     };
     for (int it = 1; it <= iters && !active.empty(); it++) {
         if (dirty) {  // one ALS iteration of the active problems as a CUDA graph

@@ -267,85 +267,6 @@ __global__ void __launch_bounds__(kThreads) k_solve_rows(C *__restrict__ M, int6
     }
 }
 
-// Fused row pass and Gram of its result: M <- M V^{-1} in place (thread per
-// row, as k_solve_rows) and the block's partial of the upper triangle of
-// Ahat^T Ahat over the rows it solved (as k_gram_partial: FP32 accumulation
-// within the block for FP32 rows, FP64 for FP64 rows), so Ahat is not read
-// back for its Gram. Blocks take 256-row chunks, grid-stride; each solved
-// row is also staged in shared memory (dynamic, 256 x (RP + 1) values) for
-// the pair sums.
-template <typename C, int RP>
-__global__ void __launch_bounds__(kThreads) k_solve_gram(C *__restrict__ M, int64_t I, int R,
-                                                         const C *__restrict__ Vinv, double *__restrict__ partial) {
-    constexpr int CC = sizeof(C) == 8 ? 16 : 32;
-    constexpr int NC = (RP + CC - 1) / CC;
-    constexpr int LDT = RP + 1;
-    __shared__ __align__(16) C Vs[MAXR][NC * CC];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *T = reinterpret_cast<C *>(smem_raw);  // kThreads x LDT
-    using A = C;  // pair sums accumulate in the row type
-    const int npairs = R * (R + 1) / 2;
-    int pr[PAIRS_PER_THREAD], ps[PAIRS_PER_THREAD];
-    A acc[PAIRS_PER_THREAD];
-#pragma unroll
-    for (int u = 0; u < PAIRS_PER_THREAD; u++) {
-        const int p = threadIdx.x + u * kThreads;
-        pr[u] = ps[u] = 0;
-        if (p < npairs) pair_of(p, R, pr[u], ps[u]);
-        acc[u] = A(0);
-    }
-    for (int idx = threadIdx.x; idx < MAXR * NC * CC; idx += kThreads) {
-        const int r = idx / (NC * CC), c = idx % (NC * CC);
-        Vs[r][c] = (r < R && c < R) ? Vinv[r * R + c] : C(0);
-    }
-    __syncthreads();
-    for (int64_t r0 = (int64_t)blockIdx.x * kThreads; r0 < I; r0 += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = r0 + threadIdx.x;
-        const int rows = (int)min((int64_t)kThreads, I - r0);
-        if (i < I) {
-            C *row = M + i * R;
-            C y[NC][CC];
-#pragma unroll
-            for (int q = 0; q < NC; q++)
-#pragma unroll
-                for (int c = 0; c < CC; c++) y[q][c] = C(0);
-#pragma unroll 1
-            for (int r = 0; r < R; r++) {
-                const C xr = row[r];
-#pragma unroll
-                for (int q = 0; q < NC; q++)
-#pragma unroll
-                    for (int c = 0; c < CC; c++) y[q][c] = fma(xr, Vs[r][q * CC + c], y[q][c]);
-            }
-#pragma unroll
-            for (int q = 0; q < NC; q++)
-#pragma unroll
-                for (int c = 0; c < CC; c++)
-                    if (q * CC + c < R) {
-                        row[q * CC + c] = y[q][c];
-                        T[threadIdx.x * LDT + q * CC + c] = y[q][c];
-                    }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < PAIRS_PER_THREAD; u++) {
-            if (threadIdx.x + u * kThreads < npairs) {
-                A sum = acc[u];
-                const C *a = T + pr[u], *bb = T + ps[u];
-#pragma unroll 4
-                for (int k = 0; k < rows; k++) sum = fma(a[k * LDT], bb[k * LDT], sum);
-                acc[u] = sum;
-            }
-        }
-        __syncthreads();  // T is rewritten by the next chunk
-    }
-#pragma unroll
-    for (int u = 0; u < PAIRS_PER_THREAD; u++) {
-        const int p = threadIdx.x + u * kThreads;
-        if (p < npairs) partial[(int64_t)blockIdx.x * npairs + p] = (double)acc[u];
-    }
-}
-
 // lambda_r = sqrt(Ghat_rr); G_n = Ghat / (lambda lambda^T); inner_r =
 // <M(:,r), A_n(:,r)> for the normalised A_n. Since M = Ahat V (Ahat = M V^{-1}),
 // <M(:,r), Ahat(:,r)> = sum_s Ghat[r][s] V[s][r], so no pass over the rows
@@ -505,7 +426,10 @@ int *gram_err_word(double *scratch) {
     return reinterpret_cast<int *>(scratch + (size_t)GR_BLOCKS * MAXPAIRS + (size_t)GR_BLOCKS * MAXR);
 }
 
+int *gram_colexp_word(double *scratch) { return reinterpret_cast<int *>(scratch + (size_t)GR_BLOCKS * MAXPAIRS); }
+
 bool gram_uses_tc(const void *A, int R, int dtype) {
+    if (dtype == RELATE_F64 || dtype == RELATE_F32) return R >= 1 && R <= MAXR;
     return dtype == RELATE_BF16 && gram_tc_supported(R) && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
 }
 
@@ -514,11 +438,16 @@ cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scra
     if (R < 1 || R > MAXR) return cudaErrorInvalidValue;
     if (I == 0) return cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
     if (gram_uses_tc(A, R, dtype)) {
-        // BF16 inputs: tcgen05 tensor cores, FP32 accumulation per block
+        // tcgen05 tensor cores: BF16 inputs directly (FP32 accumulation per
+        // block), FP64 / FP32 inputs as exact 7-bit slices (gram_oz.cu)
         const int npairs_tc = R * (R + 1) / 2;
-        const int g = gram_tc_blocks(I);
-        cudaError_t e = launch_gram_tc((const __nv_bfloat16 *)A, I, R, scratch, err ? err : gram_err_word(scratch),
-                                       wait_cycles, fault_skip, st);
+        int *e_word = err ? err : gram_err_word(scratch);
+        const bool oz = dtype != RELATE_BF16;
+        const int g = oz ? gram_oz_blocks(I) : gram_tc_blocks(I);
+        cudaError_t e = oz ? launch_gram_oz(A, I, R, dtype, scratch, gram_colexp_word(scratch), e_word, wait_cycles,
+                                            fault_skip, st)
+                           : launch_gram_tc((const __nv_bfloat16 *)A, I, R, scratch, e_word, wait_cycles, fault_skip,
+                                            st);
         if (e != cudaSuccess) return e;
         k_gram_reduce<<<(npairs_tc + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(scratch, g, R, G);
         return cudaGetLastError();
@@ -565,38 +494,6 @@ cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const do
     else
         solve_rows_rp<float>((float *)M, I, R, Vinv32, g, st);
     return cudaGetLastError();
-}
-
-template <typename C, int RP>
-static cudaError_t solve_gram_rp(C *M, int64_t I, int R, const C *Vinv, double *scratch, double *G, cudaStream_t st) {
-    const size_t smem = sizeof(C) * kThreads * (RP + 1);
-    auto kern = k_solve_gram<C, RP>;
-    cudaError_t e = allow_max_dynamic_smem(kern);
-    if (e != cudaSuccess) return e;
-    int64_t g64 = (I + kThreads - 1) / kThreads;
-    const int g = (int)(g64 > GR_BLOCKS ? GR_BLOCKS : g64);
-    kern<<<g, kThreads, smem, st>>>(M, I, R, Vinv, scratch);
-    const int npairs = R * (R + 1) / 2;
-    k_gram_reduce<<<(npairs + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(scratch, g, R, G);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_solve_gram(void *M, int64_t I, int R, int acc_dtype, const double *Vinv, const float *Vinv32,
-                              double *scratch, double *G, cudaStream_t st) {
-    if (R < 1 || R > MAXR) return cudaErrorInvalidValue;
-    if (I == 0) return cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
-    if (acc_dtype == RELATE_F64) {
-        double *m = (double *)M;
-        if (R <= 16) return solve_gram_rp<double, 16>(m, I, R, Vinv, scratch, G, st);
-        if (R <= 32) return solve_gram_rp<double, 32>(m, I, R, Vinv, scratch, G, st);
-        if (R <= 48) return solve_gram_rp<double, 48>(m, I, R, Vinv, scratch, G, st);
-        return solve_gram_rp<double, 64>(m, I, R, Vinv, scratch, G, st);
-    }
-    float *m = (float *)M;
-    if (R <= 16) return solve_gram_rp<float, 16>(m, I, R, Vinv32, scratch, G, st);
-    if (R <= 32) return solve_gram_rp<float, 32>(m, I, R, Vinv32, scratch, G, st);
-    if (R <= 48) return solve_gram_rp<float, 48>(m, I, R, Vinv32, scratch, G, st);
-    return solve_gram_rp<float, 64>(m, I, R, Vinv32, scratch, G, st);
 }
 
 cudaError_t launch_colnorms(const float *M, int64_t I, int R, double *scratch, double *lambda, cudaStream_t st) {

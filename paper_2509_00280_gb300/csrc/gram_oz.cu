@@ -1,0 +1,379 @@
+// gram_oz.cu -- G = A^T A for FP64 and FP32 matrices on the tcgen05 tensor
+// cores, by splitting every entry into exact 7-bit integer slices (the
+// splitting scheme of Ozaki et al. for accurate products on low-precision
+// multipliers).
+//
+// The Gram step of CP-ALS (the standard ALS cited in Sec. 2.2). Column r of
+// A is put on one fixed-point scale from its largest exponent field E_r
+// (k_colexp): a = q * 2^(E_r - 1077) with |q| < 2^55, q truncated toward
+// zero. |q| is cut into S slices of 7 bits, u_0 (most significant) ..
+// u_{S-1}, each carrying the sign of a, each exactly a BF16 value, so
+//   q_r q_s = sum_{i, j < S} u_i u_j 2^(7 (14 - i - j))
+// (S = 8 for FP64 inputs: q exactly; S = 4 for FP32 inputs: the top 28 bits).
+// Every pair (i, j) is a BF16 x BF16 MMA over the rows (K) accumulating in
+// FP32 in tensor memory, pairs of one group g = i + j in one accumulator.
+// A block of tensor memory holds at most 4 terms per group and row, each of
+// magnitude <= 127^2, so over a 128-row period every partial sum is an integer
+// below 2^23 and the tensor cores add exactly. After each period the groups
+// are read back (tcgen05.ld), combined exactly in 64-bit integer words and
+// added to FP64 accumulators in shared memory; the result is scaled by
+// 2^(E_r + E_s) once at the end. The products are exact; the truncation of
+// q (below 2^-55 of the column's largest magnitude per entry for S = 8, 2^-27
+// for S = 4) bounds the error of G_rs by 2^-53 sqrt(I) ||A(:, r)|| ||A(:, s)||
+// for FP64 inputs (within FP64 summation's own typical error) and by 2^-25
+// sqrt(I) ||A(:, r)|| ||A(:, s)|| for FP32 inputs.
+//
+// Operands: two 64-row stages. Slice k of a 16-row chunk is a 2 KB block of
+// the K-major layout (tcgen05.cuh) holding the 64 columns as M rows, slices
+// i and i + S/2 adjacent so that one 4 KB M = 128 operand stacks them.
+// Entries with no data (columns >= R, rows past the end) are zero.
+#include <cmath>
+
+#include "internal.cuh"
+#include "tcgen05.cuh"
+
+namespace relate {
+namespace {
+
+constexpr int OZ_THREADS = 256;
+constexpr int OZ_STAGE_ROWS = 64;
+constexpr int OZ_CHUNKS = OZ_STAGE_ROWS / 16;
+constexpr int OZ_BLK = 2048;          // one slice of one 16-row chunk: 64 (M) x 16 (K) x 2 bytes
+constexpr int OZ_BLOCKS = 152;
+constexpr int OZ_ITEMS = OZ_STAGE_ROWS / 2 * 64 / OZ_THREADS;  // (column, row pair) items per thread per stage
+
+// two stages of slices, then the FP64 accumulators [half][column][row]
+template <int S> constexpr size_t oz_smem_bytes() { return 2 * (size_t)S * OZ_CHUNKS * OZ_BLK + 2 * 64 * 64 * 8; }
+
+// Exponent field of an entry as an FP64 number (0: zero or subnormal,
+// 0x7ff: Inf or NaN), its 53-bit significand and its sign.
+template <typename T> struct OzBits;
+template <> struct OzBits<double> {
+    __device__ static int expo(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
+    __device__ static void split(double x, uint64_t &mant, int &e, uint32_t &neg) {
+        const uint64_t b = (uint64_t)__double_as_longlong(x);
+        e = (int)((b >> 52) & 0x7ff);
+        neg = (uint32_t)(b >> 63);
+        mant = (b & 0xfffffffffffffull) | (1ull << 52);
+    }
+};
+template <> struct OzBits<float> {
+    __device__ static int expo(float x) {
+        const int ef = (int)((__float_as_uint(x) >> 23) & 0xff);
+        return ef == 0 ? 0 : ef == 0xff ? 0x7ff : ef + 896;
+    }
+    __device__ static void split(float x, uint64_t &mant, int &e, uint32_t &neg) {
+        const uint32_t b = __float_as_uint(x);
+        const int ef = (int)((b >> 23) & 0xff);
+        e = ef == 0 ? 0 : ef == 0xff ? 0x7ff : ef + 896;
+        neg = b >> 31;
+        mant = (uint64_t)((b & 0x7fffffu) | 0x800000u) << 29;
+    }
+};
+
+// Largest exponent field per column of a row-major I x R matrix (R <= 64),
+// atomicMax into colexp[0..R) (zeroed by the launcher). A warp walks rows,
+// lane l holding columns l and l + 32; 8 rows per step are in flight.
+template <typename T>
+__global__ void __launch_bounds__(256) k_colexp(const T *__restrict__ A, int64_t I, int R, int *__restrict__ colexp) {
+    __shared__ int smax[64];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 64) smax[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int m0 = 0, m1 = 0;
+    const bool c0 = lane < R, c1 = lane + 32 < R;
+    for (int64_t i = w0; i < I; i += 8 * nw) {
+        T x0[8], x1[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int64_t row = i + u * nw;
+            x0[u] = (row < I && c0) ? A[row * R + lane] : T(0);
+            x1[u] = (row < I && c1) ? A[row * R + lane + 32] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            m0 = max(m0, OzBits<T>::expo(x0[u]));
+            m1 = max(m1, OzBits<T>::expo(x1[u]));
+        }
+    }
+    atomicMax(&smax[lane], m0);
+    atomicMax(&smax[lane + 32], m1);
+    __syncthreads();
+    if (threadIdx.x < R && smax[threadIdx.x] > 0) atomicMax(colexp + threadIdx.x, smax[threadIdx.x]);
+}
+
+// The S slices of one entry as BF16 bit patterns (sign on every slice).
+template <int S>
+__device__ __forceinline__ void oz_slices(uint64_t mant, int e, int E, uint32_t neg, uint32_t (&u)[S]) {
+    uint64_t q = 0;
+    if (e != 0) {
+        const int sh = max(E - e - 2, -2);  // e <= E: |q| < 2^55
+        q = sh >= 0 ? (sh < 64 ? mant >> sh : 0ull) : mant << (-sh);
+    }
+    const uint32_t sg = neg << 15;
+#pragma unroll
+    for (int k = 0; k < S; k++) {
+        const uint32_t d = (uint32_t)(q >> (7 * (7 - k))) & 127u;
+        // d as an FP32 value (exact: 2^23 + d - 2^23), whose top 16 bits are its BF16 pattern
+        const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+        u[k] = (__float_as_uint(f) >> 16) | sg;
+    }
+}
+
+// Drain of the tensor-memory blocks [C0, C1) of one pass into this thread's
+// FP64 accumulators: block c holds group g = c + OFF (OFF = 0 in the lower
+// 64 lanes, S / 2 in the upper 64). Each FP32 value is an exact integer; the
+// groups are combined exactly in 64-bit words of four groups, word k
+// weighing 2^(7 (11 - 4k)), so q_r q_s = sum_g acc_g 2^(7 (14 - g)).
+// acc points at this thread's row of [column][row] FP64 accumulators.
+template <int OFF, int C0, int C1>
+__device__ __forceinline__ void oz_drain(uint32_t tbase, double *acc) {
+    constexpr double kWordWeight[4] = {1.5111572745182865e23 /* 2^77 */, 562949953421312.0 /* 2^49 */,
+                                       2097152.0 /* 2^21 */, 0.0078125 /* 2^-7 */};
+#pragma unroll
+    for (int qc = 0; qc < 4; qc++) {  // 8 columns at a time
+        long long w[4][8];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[k][j] = 0;
+#pragma unroll
+        for (int c = C0; c < C1; c++) {
+            const int g = c + OFF, k = g >> 2, sh = 7 * (4 * k + 3 - g);
+            uint32_t v[8];
+            tc::ld8(tbase + 64u * (uint32_t)(c - C0) + 8u * (uint32_t)qc, v);
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[k][j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            double d = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if ((C0 + OFF) >> 2 <= k && k <= (C1 - 1 + OFF) >> 2) d = fma((double)w[k][j], kWordWeight[k], d);
+            acc[64 * (8 * qc + j)] += d;
+        }
+    }
+}
+
+// Per-block FP64 upper-triangle partials of A^T A (A: I x R row-major, R <=
+// 64), given colexp. With H = S / 2, the A operand of an MMA stacks slice i
+// (D lanes 0..63) over slice i + H (lanes 64..127), i < H, and the B operand
+// is slice j: one MMA forms the pairs (i, j) and (i + H, j) into tensor-memory
+// block i + j, whose lower lanes hold group i + j and upper lanes group
+// i + j + H. All S^2 pairs are formed (3H - 1 blocks; 8 at a time in 512
+// columns, so S = 8 takes a second pass over the staged slices), so the
+// products q_r q_s are exact and the only error is the truncation of q.
+// Per 128-row period: stage two 64-row buffers, MMAs, drain, per pass.
+// Waits on tensor-core commits give up after wait_cycles (then: err |= 2,
+// NaN partials); fault_skip (a test hook) issues no MMA and no commit, so
+// nothing is in flight when those waits run out.
+template <typename T, int S>
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_gram_oz(const T *__restrict__ A, int64_t I, int R, const int *__restrict__ colexp, double *__restrict__ partial,
+              int *__restrict__ err, long long wait_cycles, int fault_skip) {
+    static_assert(S == 4 || S == 8, "4 or 8 slices");
+    constexpr int H = S / 2;
+    constexpr int NCB = 3 * H - 1;                   // tensor-memory blocks of one period
+    constexpr int PA = NCB < 8 ? NCB : 8;            // blocks of the first pass
+    constexpr int STAGE_BYTES = S * OZ_CHUNKS * OZ_BLK;
+    constexpr uint32_t TMEM_COLS = 512;              // 8 blocks of 64 FP32 columns
+    extern __shared__ __align__(1024) unsigned char smem_oz[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int gave_up;
+    __shared__ int sE[64];
+    double *acc_s = reinterpret_cast<double *>(smem_oz + 2 * (size_t)STAGE_BYTES);  // [half][column][row]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int npairs = R * (R + 1) / 2;
+
+    const int64_t per = (I + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = min((int64_t)blockIdx.x * per, I);
+    const int64_t r1 = min(r0 + per, I);
+    const int nper = (int)((r1 - r0 + 2 * OZ_STAGE_ROWS - 1) / (2 * OZ_STAGE_ROWS));
+
+    if (tid < 64) sE[tid] = tid < R ? colexp[tid] : 0;
+    for (int i = tid; i < 2 * 64 * 64; i += OZ_THREADS) acc_s[i] = 0.0;
+    if (warp == 0) tc::alloc(&tmem_base, TMEM_COLS);
+    if (tid == 0) {
+        tc::mbar_init1(&bar);
+        gave_up = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = tc::instr_desc_bf16(128, R <= 32 ? 32 : 64);
+
+    // drain roles: warp (lane quarter q, column half h) reads D lanes 32q..
+    // (row r = 32 (q & 1) + lane of the lower (q < 2) or upper group set),
+    // columns 32h..; the blocks with every row above every column are skipped
+    const int q = warp & 3, hcol = warp >> 2;
+    const bool upper = q >= 2;
+    const bool drainer = ((q & 1) == 0 && (hcol == 0 || R > 32)) || ((q & 1) == 1 && hcol == 1 && R > 32);
+    const int rloc = 32 * (q & 1) + lane;
+    double *acc = acc_s + (upper ? 64 * 64 : 0) + 64 * (32 * hcol) + rloc;  // column s at acc[64 * (s - 32h)]
+    const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * hcol);
+
+    // this thread's staging items: column m, row pairs kp of a stage
+    const int m = ((tid >> 2) & 7) | (warp << 3);
+    const bool mcol = m < R;
+    const int Em = mcol ? sE[m] : 0;
+    // byte offset of slice k of chunk c in a stage: slices i and i + H of a chunk are adjacent
+    auto blk = [](int k, int c) -> uint32_t { return (uint32_t)(((c * H + (k % H)) * 2 + k / H) * OZ_BLK); };
+
+    uint32_t phase = 0;
+    bool stop = false;  // a wait gave up (the same in every thread)
+    for (int p = 0; p < nper && !stop; p++) {
+        // ---- stage 128 rows: every entry's S slices, two rows per 32-bit store
+#pragma unroll 1
+        for (int b = 0; b < 2; b++) {
+            unsigned char *buf = smem_oz + (size_t)b * STAGE_BYTES;
+            const int64_t srow = r0 + (int64_t)p * 2 * OZ_STAGE_ROWS + (int64_t)b * OZ_STAGE_ROWS;
+#pragma unroll
+            for (int it0 = 0; it0 < OZ_ITEMS; it0 += OZ_ITEMS / 2) {  // two rounds of loads in flight
+                T x[OZ_ITEMS / 2][2];
+#pragma unroll
+                for (int iu = 0; iu < OZ_ITEMS / 2; iu++) {
+                    const int kp = (tid & 3) | ((it0 + iu) << 2);
+                    const int64_t row = srow + 2 * kp;
+                    x[iu][0] = (mcol && row < r1) ? A[row * R + m] : T(0);
+                    x[iu][1] = (mcol && row + 1 < r1) ? A[(row + 1) * R + m] : T(0);
+                }
+#pragma unroll
+                for (int iu = 0; iu < OZ_ITEMS / 2; iu++) {
+                    const int kp = (tid & 3) | ((it0 + iu) << 2);
+                    const int c = kp >> 3;
+                    const uint32_t off =
+                        (uint32_t)((m >> 3) * 256 + ((kp & 7) >> 2) * 128 + (m & 7) * 16 + (kp & 3) * 4);
+                    uint32_t u0[S], u1[S];
+                    uint64_t mant;
+                    int e;
+                    uint32_t neg;
+                    OzBits<T>::split(x[iu][0], mant, e, neg);
+                    oz_slices<S>(mant, e, Em, neg, u0);
+                    OzBits<T>::split(x[iu][1], mant, e, neg);
+                    oz_slices<S>(mant, e, Em, neg, u1);
+#pragma unroll
+                    for (int k = 0; k < S; k++)
+                        *reinterpret_cast<uint32_t *>(buf + blk(k, c) + off) = u0[k] | (u1[k] << 16);
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+        __syncthreads();
+#pragma unroll 1
+        for (int pass = 0; pass < (NCB > 8 ? 2 : 1); pass++) {
+            const int c0 = pass == 0 ? 0 : 8, c1 = pass == 0 ? PA : NCB;
+            if (tid == 0) {
+                if (!fault_skip) {
+                    tc::fence_after();
+#pragma unroll 1
+                    for (int b = 0; b < 2; b++)
+#pragma unroll 1
+                        for (int c = 0; c < OZ_CHUNKS; c++)
+#pragma unroll
+                            for (int i = 0; i < H; i++) {
+                                const uint32_t base = tc::saddr(smem_oz + (size_t)b * STAGE_BYTES);
+                                const uint64_t da = tc::smem_desc(base + blk(i, c), 128, 256);
+#pragma unroll
+                                for (int j = 0; j < S; j++) {
+                                    const int cb = i + j;
+                                    if (cb < c0 || cb >= c1) continue;
+                                    const uint64_t db = tc::smem_desc(base + blk(j, c), 128, 256);
+                                    const bool fresh = b == 0 && c == 0 && i == max(0, cb - (S - 1));
+                                    tc::mma(tmem + 64u * (uint32_t)(cb - c0), da, db, idesc, fresh ? 0u : 1u);
+                                }
+                            }
+                    tc::commit(&bar);
+                }
+            }
+            // ---- drain this pass: its MMAs are complete once the commit lands
+            const bool ok = tc::mbar_wait_limit(&bar, phase, wait_cycles);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) gave_up = 1;
+                stop = true;
+                break;
+            }
+            tc::fence_after();
+            if (drainer) {
+                if (pass == 0) {
+                    if (upper) oz_drain<H, 0, PA>(tbase, acc);
+                    else oz_drain<0, 0, PA>(tbase, acc);
+                } else if constexpr (NCB > 8) {
+                    if (upper) oz_drain<H, 8, NCB>(tbase, acc);
+                    else oz_drain<0, 8, NCB>(tbase, acc);
+                }
+            }
+            tc::fence_before();
+            __syncthreads();  // the next MMAs overwrite the accumulators
+        }
+    }
+    __syncthreads();
+    tc::fence_after();
+    if (gave_up) {  // a tensor-core commit never arrived: poison this block's partials and report
+        if (tid == 0) atomicOr(err, 2);
+        for (int pp = tid; pp < npairs; pp += OZ_THREADS)
+            partial[(int64_t)blockIdx.x * npairs + pp] = __longlong_as_double(0x7ff8000000000000ll);
+    } else {
+        // G_rs = 2^(E_r + E_s - 2154) q_r q_s, a = q 2^(E - 1077)
+        for (int pp = tid; pp < npairs; pp += OZ_THREADS) {
+            int r = 0, left = pp;
+            while (left >= R - r) {
+                left -= R - r;
+                r++;
+            }
+            const int s2 = r + left;
+            const int Er = sE[r], Es = sE[s2];
+            double g;
+            if (Er >= 0x7ff || Es >= 0x7ff) g = __longlong_as_double(0x7ff8000000000000ll);
+            else if (Er == 0 || Es == 0) g = 0.0;
+            else g = ldexp(acc_s[64 * s2 + r] + acc_s[64 * 64 + 64 * s2 + r], Er + Es - 2154);
+            partial[(int64_t)blockIdx.x * npairs + pp] = g;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tmem, TMEM_COLS);
+}
+
+template <typename T, int S>
+cudaError_t launch_oz(const T *A, int64_t I, int R, double *partial, int *colexp, int *err, long long wait_cycles,
+                      int fault_skip, int g, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(colexp, 0, 64 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int64_t gw = (I + 8 * 8 - 1) / (8 * 8);  // 8 warps per block, 8 rows in flight per warp
+    const int g1 = (int)(gw > 152 * 4 ? 152 * 4 : gw < 1 ? 1 : gw);
+    k_colexp<T><<<g1, 256, 0, st>>>(A, I, R, colexp);
+    auto kern = k_gram_oz<T, S>;
+    if ((e = allow_max_dynamic_smem(kern)) != cudaSuccess) return e;
+    kern<<<g, OZ_THREADS, oz_smem_bytes<S>(), st>>>(A, I, R, colexp, partial, err,
+                                                    wait_cycles > 0 ? wait_cycles : kWaitCycles, fault_skip);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int gram_oz_blocks(int64_t I) {
+    int64_t g = (I + OZ_STAGE_ROWS - 1) / OZ_STAGE_ROWS;
+    if (g > OZ_BLOCKS) g = OZ_BLOCKS;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t launch_gram_oz(const void *A, int64_t I, int R, int dtype, double *partial, int *colexp, int *err,
+                           long long wait_cycles, int fault_skip, cudaStream_t st) {
+    if (R < 1 || R > 64) return cudaErrorInvalidValue;
+    const int g = gram_oz_blocks(I);
+    if (dtype == RELATE_F64)
+        return launch_oz<double, 8>((const double *)A, I, R, partial, colexp, err, wait_cycles, fault_skip, g, st);
+    if (dtype == RELATE_F32)
+        return launch_oz<float, 4>((const float *)A, I, R, partial, colexp, err, wait_cycles, fault_skip, g, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace relate

@@ -9,10 +9,10 @@
 // first 64 rows of the same tile. BF16 x BF16 products are exact in FP32;
 // accumulation is FP32 in tensor memory within a block and FP64 across blocks.
 //
-// Shared-memory operand layout: K-major "core matrices" (8 rows x 16 bytes)
-// without swizzling; a 16-row chunk is 16 M-groups x 2 K-groups of cores:
-// byte(m, k) = (m / 8) * 256 + (k / 8) * 128 + (m % 8) * 16 + (k % 8) * 2.
+// Shared-memory operand layout: K-major core matrices without swizzling
+// (tcgen05.cuh); a 16-row chunk is 16 M-groups x 2 K-groups of cores.
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace relate {
 namespace {
@@ -27,72 +27,7 @@ constexpr int TC_M = 128, TC_N = 64;
 constexpr int TC_TMEM_COLS = 64;          // FP32 accumulator columns (N)
 constexpr int TC_BLOCKS = 152;
 
-__device__ __forceinline__ uint32_t saddr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-// tcgen05 shared-memory matrix descriptor: K-major, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3fff);
-    d |= (uint64_t)((lbo >> 4) & 0x3fff) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3fff) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for this generation
-    return d;                // base offset 0, layout type 0 (no swizzle)
-}
-
-// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major.
-__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
-    return (1u << 4)                      // D format: F32
-           | (1u << 7)                    // A format: BF16
-           | (1u << 10)                   // B format: BF16
-           | ((uint32_t)(N >> 3) << 17)   // N / 8
-           | ((uint32_t)(M >> 4) << 24);  // M / 16
-}
-
-__device__ __forceinline__ void mbar_init1(uint64_t *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(saddr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait (`limit` SM clock cycles); false when it gave up.
-__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity, long long limit) {
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try(bar, parity))
-        if (clock64() - t0 > limit) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(accum)
-        : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
-                 : "memory");
-}
-
-// 32 lanes x 32 columns of FP32 from tensor memory (this warp's lane quarter).
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+using namespace tc;
 
 // Per-block upper-triangle partials (FP64) of A^T A, A BF16 I x R (R <= 64,
 // R % 8 == 0 so a row is a whole number of 16-byte vectors). Every wait on a
@@ -169,9 +104,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const __nv_bfloat16 *
             for (int cc = 0; cc < TC_CHUNKS; cc++) {
                 const uint32_t a_addr = saddr(buf + (size_t)cc * TC_CHUNK_BYTES);
                 const uint64_t da = smem_desc(a_addr, 128, 256);
-                tc_mma(tmem, da, da, idesc, (s > 0 || cc > 0) ? 1u : 0u);
+                mma(tmem, da, da, idesc, (s > 0 || cc > 0) ? 1u : 0u);
             }
-            tc_commit(&bar[b]);
+            commit(&bar[b]);
         }
         issued[b] = 1;
     }
@@ -189,7 +124,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gram_tc(const __nv_bfloat16 *
         // warp w holds D rows 32w..32w+31 (lane = row), columns 0..63
         uint32_t v[32];
         for (int half = 0; half < 2; half++) {
-            tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * half), v);
+            ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * half), v);
             const int r = 32 * warp + lane;
             if (r < R) {
                 for (int j = 0; j < 32; j++) {

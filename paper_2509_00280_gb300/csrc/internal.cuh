@@ -218,8 +218,9 @@ int mttkrp_acc_bytes(int factor_dtype);
 // the row passes.
 size_t dense_scratch_doubles(int R);
 
-// G = A^T A, FP64 out (R x R) via per-block partials in `scratch`. BF16
-// inputs (gram_uses_tc) run on the tensor cores, whose bounded waits report a
+// G = A^T A, FP64 out (R x R) via per-block partials in `scratch`. FP64,
+// FP32 and aligned BF16 inputs with R % 8 == 0 (gram_uses_tc) run on the
+// tensor cores, whose bounded waits report a
 // timeout as *err |= 2 (err = null: the status word inside `scratch`,
 // gram_err_word) and NaN partials; wait_cycles <= 0 = kWaitCycles;
 // fault_skip (a test hook) issues no tensor-core work, so the waits run out.
@@ -236,6 +237,15 @@ int gram_tc_blocks(int64_t I);
 cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err,
                            long long wait_cycles, int fault_skip, cudaStream_t st);
 
+// Tensor-core Gram partials for FP64 (8 slices) or FP32 (4 slices) A, R <=
+// 64, any alignment of the element type: k_colexp writes the columns'
+// largest exponent fields to colexp[0..64) (zeroed first), then one FP64
+// upper-triangle partial per block (gram_oz_blocks(I) blocks); err |= 2 and
+// NaN partials if a bounded wait on the tensor cores gave up.
+int gram_oz_blocks(int64_t I);
+cudaError_t launch_gram_oz(const void *A, int64_t I, int R, int dtype, double *partial, int *colexp, int *err,
+                           long long wait_cycles, int fault_skip, cudaStream_t st);
+
 // V = Hadamard_{k != n} G_k (kept in Vsave); FP64 Cholesky; V^{-1} in FP64
 // (f64_apply) or FP32 (Vinv32, always written).
 // status[0] |= 1 on ridge retry, status[1] = 1 if not PD after the retry.
@@ -243,10 +253,6 @@ cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *V
                              double *Vsave, int f64_apply, int *status, cudaStream_t st);
 
 // In place, M (I x R, acc dtype) <- M V^{-1}.
-// launch_solve_rows followed by the Gram of the result into G (R x R FP64),
-// in one pass over the rows (the FP32/FP64 factor path).
-cudaError_t launch_solve_gram(void *M, int64_t I, int R, int acc_dtype, const double *Vinv, const float *Vinv32,
-                              double *scratch, double *G, cudaStream_t st);
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv,
                               const float *Vinv32, cudaStream_t st);
 

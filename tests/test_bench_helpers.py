@@ -40,7 +40,7 @@ def test_kernel_sha_ignores_comments(tmp_path, monkeypatch):
     import shutil
     src = tmp_path / "paper_2509_00280_gb300" / "csrc"
     src.mkdir(parents=True)
-    for name in ("mttkrp_impl.cuh", "mttkrp.cu"):
+    for name in ("mttkrp_impl.cuh", "mttkrp.cu", "mttkrp_fac.cuh"):
         shutil.copy(f"{ROOT}/paper_2509_00280_gb300/csrc/{name}", src / name)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     a = bench._kernel_sha()

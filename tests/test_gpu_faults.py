@@ -9,8 +9,9 @@ RELATE_FAULT is the library's host-side test hook:
   handle's error flag and returns, and the host reads RELATE_ERR_TIMEOUT
   (relate_sync_status, relate_cpals). No trap, no fault: the context stays
   usable and the next MTTKRP (hook unset) matches the oracle.
-* "gram_timeout": the tensor-core Gram (BF16 factors) issues no MMA and
-  waits for their completion with the same short limit; relate_gram and
+* "gram_timeout": the tensor-core Gram (BF16 inputs directly, FP32 / FP64
+  inputs as integer slices) issues no MMA and waits for their completion
+  with the same short limit; relate_gram and
   relate_cpals report RELATE_ERR_TIMEOUT, and with the hook unset the same
   calls succeed.
 """
@@ -69,25 +70,26 @@ def test_injected_timeout_is_reported_and_the_context_stays_usable(monkeypatch):
     h.close()
 
 
-def test_injected_tensor_core_gram_timeout_is_reported(monkeypatch):
+@pytest.mark.parametrize("dt", ["bf16", "f32", "f64"])
+def test_injected_tensor_core_gram_timeout_is_reported(monkeypatch, dt):
     rng = np.random.default_rng(31)
-    A = torch.from_numpy(rng.random((20000, 32))).to("cuda").to(torch.bfloat16).contiguous()
+    A = factors_dev([rng.random((20000, 32))], dt)[0]
     G = torch.empty((32, 32), dtype=torch.float64, device="cuda")
     monkeypatch.setenv("RELATE_FAULT", "gram_timeout")
     with pytest.raises(rl.RelateError) as ei:
-        rl.relate_gram(A, 32, "bf16", G)
+        rl.relate_gram(A, 32, dt, G)
     assert ei.value.status == TIMEOUT
     spec, c, v = _small()
     fs = synth.init_factors(spec.dims, 16, seed=0, dtype=np.float32)
-    h = encode_dev(c, v, spec.dims, factor_dtype="bf16")
+    h = encode_dev(c, v, spec.dims, factor_dtype=dt)
     with pytest.raises(rl.RelateError) as ei:
-        rl.relate_cpals(h, 16, 2, 0.0, factors_dev(fs, "bf16"))
+        rl.relate_cpals(h, 16, 2, 0.0, factors_dev(fs, dt))
     assert ei.value.status == TIMEOUT
     monkeypatch.delenv("RELATE_FAULT")
-    rl.relate_gram(A, 32, "bf16", G)
+    rl.relate_gram(A, 32, dt, G)
     torch.cuda.synchronize()
     exact = A.to(torch.float64).T @ A.to(torch.float64)
-    assert float(torch.linalg.norm(G - exact) / torch.linalg.norm(exact)) <= 2e-5
-    res = rl.relate_cpals(h, 16, 2, 0.0, factors_dev(fs, "bf16"))
+    assert float(torch.linalg.norm(G - exact) / torch.linalg.norm(exact)) <= (1e-13 if dt == "f64" else 2e-5)
+    res = rl.relate_cpals(h, 16, 2, 0.0, factors_dev(fs, dt))
     assert res["status"] == 0 and np.isfinite(res["fit"])
     h.close()
