@@ -371,6 +371,33 @@ def _roofline(per_mode, fdt, workload):
             "traffic": traffic, "peak_kind": kind, "kernel": "k_mttkrp", "per_mode": per_mode}
 
 
+def _time_dense(rl, torch, dev, I, R, fdt, reps):
+    """CUDA-event time of relate_solve_rows and relate_gram on a random I x R
+    matrix (each call includes its status read, one host sync)."""
+    tdt = {"f64": torch.float64, "f32": torch.float32}[fdt if fdt in ("f64", "f32") else "f32"]
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    M = torch.rand((I, R), generator=g, device=dev, dtype=torch.float64).to(tdt)
+    W = torch.rand((R, R), generator=g, device=dev, dtype=torch.float64) / R
+    G = torch.empty((R, R), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    dt = "f64" if tdt == torch.float64 else "f32"
+    out = {"only_dense": I, "R": R, "dtype": dt}
+    for name, fn in (("solve_rows_ms", lambda: rl.relate_solve_rows(M, R, dt, W, st)),
+                     ("gram_ms", lambda: rl.relate_gram(M, R, dt, G, st))):
+        fn()
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        out[name] = round(min(t), 3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,6 +419,10 @@ def main():
                     help="with --only-kernel: fiber-factoring depth of every mode (relate_set_mode_plan)")
     ap.add_argument("--col-passes", type=int, default=0,
                     help="with --only-kernel: column passes of every mode (relate_set_mode_plan)")
+    ap.add_argument("--only-dense", action="store_true",
+                    help="time only the dense row update and Gram (relate_solve_rows, relate_gram) on a random "
+                         "I x R matrix, I = the workload's longest mode (profiling runs)")
+    ap.add_argument("--dense-rows", type=int, default=0, help="with --only-dense: I instead of the longest mode")
     args = ap.parse_args()
 
     dist, world, rank, local = _dist_setup()
@@ -424,6 +455,9 @@ def main():
     import paper_2509_00280_gb300 as rl
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only_dense:
+        print(json.dumps(_time_dense(rl, torch, dev, args.dense_rows or max(spec.dims), R, fdt, max(1, args.steps))))
+        return
     t_gen = time.perf_counter()
     _, coords, vals = _load_workload(args.workload)
     t_gen = time.perf_counter() - t_gen

@@ -397,13 +397,39 @@ int relate_get_partitions(relate_handle_t h, uint32_t *lo, uint32_t *hi, void *s
 
 /* G = A^T A (the Gram step of CP-ALS, the standard ALS cited in Sec. 2.2)
  * for a DEVICE matrix A (I x R, row-major, dtype F64/F32/BF16), written to
- * DEVICE G (R x R FP64). FP64 inputs accumulate in FP64; FP32 and BF16 inputs
- * accumulate in FP32 within blocks of rows and in FP64 across blocks. BF16
- * inputs with R % 8 == 0 and a 16-byte aligned A run on the tensor cores;
- * that path synchronises `stream` once to read the kernel's bounded-wait
- * status. Otherwise asynchronous on stream. Errors: INVALID_ARG, OOM,
- * TIMEOUT (a tensor-core wait ran out; G is then NaN), CUDA. */
+ * DEVICE G (R x R FP64). All paths use the tensor cores except BF16 inputs
+ * with R % 8 != 0 or an A not 16-byte aligned:
+ * - FP64 / FP32 A (any element alignment): every entry as exact signed 7-bit
+ *   integer slices on its column's scale (8 slices for FP64, 4 for FP32),
+ *   all slice products formed as BF16 MMAs whose FP32 sums stay exact
+ *   integers, combined in 64-bit integers and FP64. The only error is the
+ *   truncation of each entry below 2^-55 (FP64) or 2^-27 (FP32) of its
+ *   column's largest magnitude: |G_rs - exact| <= 2^-53 sqrt(I) |A_r| |A_s|
+ *   (FP64) or 2^-25 sqrt(I) |A_r| |A_s| (FP32), |A_r| the column norms. A
+ *   column holding Inf or NaN gives NaN entries; subnormal entries count as 0.
+ * - BF16 A with R % 8 == 0 and 16-byte aligned: BF16 MMAs, FP32 accumulation
+ *   within blocks of rows, FP64 across blocks; otherwise FP32 accumulation
+ *   on the FP32 pipe within blocks of rows.
+ * The tensor-core paths synchronise `stream` once to read the kernel's
+ * bounded-wait status; otherwise asynchronous on stream. Errors:
+ * INVALID_ARG, OOM, TIMEOUT (a tensor-core wait ran out; G is then NaN),
+ * CUDA. */
 int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G, void *stream);
+
+/* In place M <- M W: the row update A_n = M V^{-1} of CP-ALS (the standard
+ * ALS cited in Sec. 2.2) with W = V^{-1}, for a DEVICE matrix M (I x R,
+ * row-major, dtype F64 or F32, 1 <= R <= 64) and a DEVICE W (R x R
+ * row-major FP64). FP64 runs on the tensor cores: each row of M on its own
+ * scale and each column of W on its own, as exact signed 7-bit integer
+ * slices, all 64 slice products as BF16 MMAs with exact integer FP32 sums,
+ * the dot products formed exactly in 128-bit integers and rounded once to
+ * FP64; the only errors are the truncations of the entries (below 2^-55 of
+ * their row's / column's largest magnitude): |error| <= 2^-53 R
+ * max_r |M_ir| max_r |W_rs| plus the rounding. FP32 M is multiplied by W
+ * rounded to FP32 on the FP32 pipe. Synchronises `stream` once. Errors:
+ * INVALID_ARG, OOM, TIMEOUT (a tensor-core wait ran out; rows may be left
+ * unchanged), CUDA. */
+int relate_solve_rows(void *M, int64_t I, int R, relate_dtype_t dtype, const double *W, void *stream);
 
 /* The same Gram step as relate_gram, for callers that cannot allocate device
  * memory when they call it: applications that hand all device memory to

@@ -588,6 +588,14 @@ int run_mttkrp_batch(const BatchItemRef *items, int n, cudaStream_t st) {
 // normalised Gram, so that it overlaps that mode's factor store and this
 // mode's MTTKRP (the BF16 path forms the Gram from the stored factor, so
 // it forks at the start of the mode).
+// The row pass A = M V^{-1} of mode update with the gram_timeout test hook
+// applied (the FP64 row pass runs on the tensor cores too).
+cudaError_t solve_checked(relate_handle_s *h, int64_t In, int R, cudaStream_t st) {
+    const bool f = fault_is("gram_timeout");
+    return launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_err, st, f ? 100000000LL : 0,
+                             f ? 1 : 0);
+}
+
 bool tc_path_of(const relate_handle_s *h, int R) { return h->factor_dtype == RELATE_BF16 && gram_tc_supported(R); }
 
 cudaError_t fork_normal_eq(relate_handle_s *h, int R, int m) {
@@ -621,7 +629,7 @@ int mode_post(relate_handle_s *h, int R, int n, void *const *factors) {
     if (tc_path) {
         // lambda from Ahat's column norms, store the normalised BF16 factor,
         // then its Gram on the tensor cores (of the stored values)
-        if ((e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess ||
+        if ((e = solve_checked(h, In, R, st)) != cudaSuccess ||
             (e = launch_colnorms((const float *)h->d_M, In, R, h->d_scratch, h->d_lambda, st)) != cudaSuccess ||
             (e = launch_scale_store(h->d_M, In, R, h->acc_dtype, h->d_lambda, factors[n], h->factor_dtype, st)) !=
                 cudaSuccess ||
@@ -634,7 +642,7 @@ int mode_post(relate_handle_s *h, int R, int n, void *const *factors) {
     // the row pass and the Gram of its result (tensor cores), then finish,
     // have consumed V^{-1} and V: the next mode's normal equations may
     // overwrite them
-    if ((e = launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, st)) != cudaSuccess ||
+    if ((e = solve_checked(h, In, R, st)) != cudaSuccess ||
         (e = gram_checked(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, h->d_err, st)) != cudaSuccess ||
         (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals: mode update");
@@ -1633,6 +1641,31 @@ int relate_gram(const void *A, int64_t I, int R, relate_dtype_t dtype, double *G
     if (e != cudaSuccess) return cuda_fail(e, "relate_gram: launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "relate_gram: free");
     if (flag) return fail(RELATE_ERR_TIMEOUT, "relate_gram: a bounded tensor-core wait timed out (G is NaN)");
+    return RELATE_OK;
+}
+
+int relate_solve_rows(void *M, int64_t I, int R, relate_dtype_t dtype, const double *W, void *stream) {
+    g_err[0] = 0;
+    if ((!M && I > 0) || !W || I < 0 || R < 1 || R > RELATE_MAX_RANK || (dtype != RELATE_F64 && dtype != RELATE_F32))
+        return fail(RELATE_ERR_INVALID_ARG, "relate_solve_rows: bad argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (I == 0) return RELATE_OK;
+    void *scratch = nullptr;  // status word, then W in FP32
+    cudaError_t e = dalloc(&scratch, 16 + (size_t)R * R * 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_solve_rows: scratch");
+    int *err = (int *)scratch;
+    float *W32 = (float *)((char *)scratch + 16);
+    const bool f = fault_is("gram_timeout");
+    int flag = 0;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), st)) == cudaSuccess &&
+        (dtype == RELATE_F64 || (e = launch_to_float(W, R * R, W32, st)) == cudaSuccess) &&
+        (e = launch_solve_rows(M, I, R, dtype, W, W32, err, st, f ? 100000000LL : 0, f ? 1 : 0)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaError_t e2 = cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "relate_solve_rows: launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "relate_solve_rows: free");
+    if (flag) return fail(RELATE_ERR_TIMEOUT, "relate_solve_rows: a bounded tensor-core wait timed out");
     return RELATE_OK;
 }
 

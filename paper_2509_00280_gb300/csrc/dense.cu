@@ -485,14 +485,22 @@ static void solve_rows_rp(C *M, int64_t I, int R, const C *Vinv, int g, cudaStre
 }
 
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv, const float *Vinv32,
-                              cudaStream_t st) {
+                              int *err, cudaStream_t st, long long wait_cycles, int fault_skip) {
     if (I == 0) return cudaSuccess;
+    if (acc_dtype == RELATE_F64)  // tensor cores, exact integer slices (solve_oz.cu)
+        return launch_solve_oz((double *)M, I, R, Vinv, err, wait_cycles, fault_skip, st);
     int64_t g64 = (I + kThreads - 1) / kThreads;
     const int g = (int)(g64 > 152 * 8 ? 152 * 8 : g64);
-    if (acc_dtype == RELATE_F64)
-        solve_rows_rp<double>((double *)M, I, R, Vinv, g, st);
-    else
-        solve_rows_rp<float>((float *)M, I, R, Vinv32, g, st);
+    solve_rows_rp<float>((float *)M, I, R, Vinv32, g, st);
+    return cudaGetLastError();
+}
+
+__global__ void k_to_float(const double *__restrict__ x, int n, float *__restrict__ y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = (float)x[i];
+}
+
+cudaError_t launch_to_float(const double *x, int n, float *y, cudaStream_t st) {
+    k_to_float<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(x, n, y);
     return cudaGetLastError();
 }
 

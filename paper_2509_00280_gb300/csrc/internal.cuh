@@ -252,9 +252,19 @@ cudaError_t launch_gram_oz(const void *A, int64_t I, int R, int dtype, double *p
 cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *Vinv, float *Vinv32,
                              double *Vsave, int f64_apply, int *status, cudaStream_t st);
 
-// In place, M (I x R, acc dtype) <- M V^{-1}.
+// In place, M (I x R, acc dtype) <- M V^{-1}. FP64 runs on the tensor cores
+// (launch_solve_oz), whose bounded waits report a timeout as *err |= 2;
+// FP32 on the FP32 pipe.
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv,
-                              const float *Vinv32, cudaStream_t st);
+                              const float *Vinv32, int *err, cudaStream_t st, long long wait_cycles = 0,
+                              int fault_skip = 0);
+// y[i] = (float)x[i], i < n.
+cudaError_t launch_to_float(const double *x, int n, float *y, cudaStream_t st);
+// In place M <- M W, FP64, R <= 64, as exact 7-bit integer slices on the
+// tensor cores; err |= 2 if a bounded wait gave up (wait_cycles <= 0:
+// kWaitCycles); fault_skip (a test hook) issues no tensor-core work.
+cudaError_t launch_solve_oz(double *M, int64_t I, int R, const double *W, int *err, long long wait_cycles,
+                            int fault_skip, cudaStream_t st);
 
 // lambda and the normalised Gram G_n from the raw Gram of M V^{-1} (in G_n),
 // and the fit inner products from that Gram and V.

@@ -92,6 +92,7 @@ def lib():
                 "relate_get_partitions": (I, [P, P, P, P]),
                 "relate_gram": (I, [P, I64, I, I, P, P]),
                 "relate_gram_noalloc": (I, [P, I64, I, I, P, P]),
+                "relate_solve_rows": (I, [P, I64, I, I, P, P]),
                 "relate_sync_status": (I, [P, P]),
                 "relate_free": (None, [P]),
                 "relate_status_string": (ctypes.c_char_p, [I]),
@@ -421,6 +422,13 @@ def relate_get_partitions(h: Handle, lo, hi, stream=None) -> None:
 def relate_gram(A, R: int, dtype, G, stream=None) -> None:
     I = int(A.shape[0]) if A is not None else 0
     _check(lib().relate_gram(_ptr(A), I, int(R), _DTYPES[dtype], _ptr(G), _stream(stream)), "relate_gram")
+
+
+def relate_solve_rows(M, R: int, dtype, W, stream=None) -> None:
+    """In place M <- M W (the CP-ALS row update with W = V^{-1}); M (I x R)
+    F64 or F32 on the device, W (R x R) FP64 on the device."""
+    I = int(M.shape[0]) if M is not None else 0
+    _check(lib().relate_solve_rows(_ptr(M), I, int(R), _DTYPES[dtype], _ptr(W), _stream(stream)), "relate_solve_rows")
 
 
 def relate_sync_status(h: Handle, stream=None) -> None:
