@@ -399,14 +399,16 @@ int relate_get_partitions(relate_handle_t h, uint32_t *lo, uint32_t *hi, void *s
  * for a DEVICE matrix A (I x R, row-major, dtype F64/F32/BF16), written to
  * DEVICE G (R x R FP64). All paths use the tensor cores except BF16 inputs
  * with R % 8 != 0 or an A not 16-byte aligned:
- * - FP64 / FP32 A (any element alignment): every entry as exact signed 7-bit
- *   integer slices on its column's scale (8 slices for FP64, 4 for FP32),
- *   all slice products formed as BF16 MMAs whose FP32 sums stay exact
- *   integers, combined in 64-bit integers and FP64. The only error is the
- *   truncation of each entry below 2^-55 (FP64) or 2^-27 (FP32) of its
- *   column's largest magnitude: |G_rs - exact| <= 2^-53 sqrt(I) |A_r| |A_s|
- *   (FP64) or 2^-25 sqrt(I) |A_r| |A_s| (FP32), |A_r| the column norms. A
- *   column holding Inf or NaN gives NaN entries; subnormal entries count as 0.
+ * - FP64 A (any 8-byte alignment): every entry as exact signed 7-bit integer
+ *   slices on its column's scale, all slice products formed as BF16 MMAs
+ *   whose FP32 sums stay exact integers, combined in 64-bit integers and
+ *   FP64. The only error is the truncation of each entry below 2^-55 of its
+ *   column's largest magnitude: |G_rs - exact| <= 2^-53 sqrt(I) |A_r| |A_s|,
+ *   |A_r| the column norms. A column holding Inf or NaN gives NaN entries;
+ *   subnormal entries count as 0.
+ * - FP32 A (any 4-byte alignment): every entry as three BF16 terms, the
+ *   products that matter at FP32 precision as BF16 MMAs, FP32 accumulation
+ *   over at most 2048 rows, FP64 beyond.
  * - BF16 A with R % 8 == 0 and 16-byte aligned: BF16 MMAs, FP32 accumulation
  *   within blocks of rows, FP64 across blocks; otherwise FP32 accumulation
  *   on the FP32 pipe within blocks of rows.

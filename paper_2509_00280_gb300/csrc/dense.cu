@@ -438,16 +438,22 @@ cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scra
     if (R < 1 || R > MAXR) return cudaErrorInvalidValue;
     if (I == 0) return cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
     if (gram_uses_tc(A, R, dtype)) {
-        // tcgen05 tensor cores: BF16 inputs directly (FP32 accumulation per
-        // block), FP64 / FP32 inputs as exact 7-bit slices (gram_oz.cu)
+        // tcgen05 tensor cores: BF16 inputs directly, FP32 inputs as three
+        // BF16 terms (gram_f32.cu), FP64 inputs as exact 7-bit slices (gram_oz.cu)
         const int npairs_tc = R * (R + 1) / 2;
         int *e_word = err ? err : gram_err_word(scratch);
-        const bool oz = dtype != RELATE_BF16;
-        const int g = oz ? gram_oz_blocks(I) : gram_tc_blocks(I);
-        cudaError_t e = oz ? launch_gram_oz(A, I, R, dtype, scratch, gram_colexp_word(scratch), e_word, wait_cycles,
-                                            fault_skip, st)
-                           : launch_gram_tc((const __nv_bfloat16 *)A, I, R, scratch, e_word, wait_cycles, fault_skip,
-                                            st);
+        int g;
+        cudaError_t e;
+        if (dtype == RELATE_F64) {
+            g = gram_oz_blocks(I);
+            e = launch_gram_oz(A, I, R, dtype, scratch, gram_colexp_word(scratch), e_word, wait_cycles, fault_skip, st);
+        } else if (dtype == RELATE_F32) {
+            g = gram_f32_blocks(I);
+            e = launch_gram_f32((const float *)A, I, R, scratch, e_word, wait_cycles, fault_skip, st);
+        } else {
+            g = gram_tc_blocks(I);
+            e = launch_gram_tc((const __nv_bfloat16 *)A, I, R, scratch, e_word, wait_cycles, fault_skip, st);
+        }
         if (e != cudaSuccess) return e;
         k_gram_reduce<<<(npairs_tc + kThreads / 32 - 1) / (kThreads / 32), kThreads, 0, st>>>(scratch, g, R, G);
         return cudaGetLastError();

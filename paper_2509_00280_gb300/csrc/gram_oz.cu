@@ -1,5 +1,5 @@
-// gram_oz.cu -- G = A^T A for FP64 and FP32 matrices on the tcgen05 tensor
-// cores, by splitting every entry into exact 7-bit integer slices (the
+// gram_oz.cu -- G = A^T A for FP64 matrices on the tcgen05 tensor cores,
+// by splitting every entry into exact 7-bit integer slices (the
 // splitting scheme of Ozaki et al. for accurate products on low-precision
 // multipliers).
 //
@@ -7,9 +7,9 @@
 // A is put on one fixed-point scale from its largest exponent field E_r
 // (k_colexp): a = q * 2^(E_r - 1077) with |q| < 2^55, q truncated toward
 // zero. |q| is cut into S slices of 7 bits, u_0 (most significant) ..
-// u_{S-1}, each carrying the sign of a, each exactly a BF16 value, so
-//   q_r q_s = sum_{i, j < S} u_i u_j 2^(7 (14 - i - j))
-// (S = 8 for FP64 inputs: q exactly; S = 4 for FP32 inputs: the top 28 bits).
+// u_{S-1} (S = 8: q exactly), each carrying the sign of a, each exactly a
+// BF16 value, so
+//   q_r q_s = sum_{i, j < S} u_i u_j 2^(7 (14 - i - j)).
 // Every pair (i, j) is a BF16 x BF16 MMA over the rows (K) accumulating in
 // FP32 in tensor memory, pairs of one group g = i + j in one accumulator.
 // A block of tensor memory holds at most 4 terms per group and row, each of
@@ -18,10 +18,9 @@
 // are read back (tcgen05.ld), combined exactly in 64-bit integer words and
 // added to FP64 accumulators in shared memory; the result is scaled by
 // 2^(E_r + E_s) once at the end. The products are exact; the truncation of
-// q (below 2^-55 of the column's largest magnitude per entry for S = 8, 2^-27
-// for S = 4) bounds the error of G_rs by 2^-53 sqrt(I) ||A(:, r)|| ||A(:, s)||
-// for FP64 inputs (within FP64 summation's own typical error) and by 2^-25
-// sqrt(I) ||A(:, r)|| ||A(:, s)|| for FP32 inputs.
+// q (below 2^-55 of the column's largest magnitude per entry) bounds the
+// error of G_rs by 2^-53 sqrt(I) ||A(:, r)|| ||A(:, s)||, within FP64
+// summation's own typical error.
 //
 // Operands: two 64-row stages. Slice k of a 16-row chunk is a 2 KB block of
 // the K-major layout (tcgen05.cuh) holding the 64 columns as M rows, slices
@@ -55,19 +54,6 @@ template <> struct OzBits<double> {
         e = (int)((b >> 52) & 0x7ff);
         neg = (uint32_t)(b >> 63);
         mant = (b & 0xfffffffffffffull) | (1ull << 52);
-    }
-};
-template <> struct OzBits<float> {
-    __device__ static int expo(float x) {
-        const int ef = (int)((__float_as_uint(x) >> 23) & 0xff);
-        return ef == 0 ? 0 : ef == 0xff ? 0x7ff : ef + 896;
-    }
-    __device__ static void split(float x, uint64_t &mant, int &e, uint32_t &neg) {
-        const uint32_t b = __float_as_uint(x);
-        const int ef = (int)((b >> 23) & 0xff);
-        e = ef == 0 ? 0 : ef == 0xff ? 0x7ff : ef + 896;
-        neg = b >> 31;
-        mant = (uint64_t)((b & 0x7fffffu) | 0x800000u) << 29;
     }
 };
 
@@ -133,7 +119,13 @@ __device__ __forceinline__ void oz_drain(uint32_t tbase, double *acc) {
     constexpr double kWordWeight[4] = {1.5111572745182865e23 /* 2^77 */, 562949953421312.0 /* 2^49 */,
                                        2097152.0 /* 2^21 */, 0.0078125 /* 2^-7 */};
 #pragma unroll
-    for (int qc = 0; qc < 4; qc++) {  // 8 columns at a time
+    for (int qc = 0; qc < 4; qc++) {  // 8 columns at a time, all blocks of the pass in flight
+        uint32_t va[32], vb[32];
+#pragma unroll
+        for (int c = C0; c < C1; c++)
+            tc::ld8_nowait(tbase + 64u * (uint32_t)(c - C0) + 8u * (uint32_t)qc, (c - C0 < 4 ? va : vb) + 8 * ((c - C0) & 3));
+        tc::wait_ld32(va);
+        tc::wait_ld32(vb);
         long long w[4][8];
 #pragma unroll
         for (int k = 0; k < 4; k++)
@@ -142,8 +134,7 @@ __device__ __forceinline__ void oz_drain(uint32_t tbase, double *acc) {
 #pragma unroll
         for (int c = C0; c < C1; c++) {
             const int g = c + OFF, k = g >> 2, sh = 7 * (4 * k + 3 - g);
-            uint32_t v[8];
-            tc::ld8(tbase + 64u * (uint32_t)(c - C0) + 8u * (uint32_t)qc, v);
+            const uint32_t *v = (c - C0 < 4 ? va : vb) + 8 * ((c - C0) & 3);
 #pragma unroll
             for (int j = 0; j < 8; j++) w[k][j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
         }
@@ -277,13 +268,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         for (int c = 0; c < OZ_CHUNKS; c++)
 #pragma unroll
                             for (int i = 0; i < H; i++) {
-                                const uint32_t base = tc::saddr(smem_oz + (size_t)b * STAGE_BYTES);
-                                const uint64_t da = tc::smem_desc(base + blk(i, c), 128, 256);
+                                // descriptors differ only in the start address field (address >> 4)
+                                const uint64_t d0 = tc::smem_desc(tc::saddr(smem_oz + (size_t)b * STAGE_BYTES), 128, 256);
+                                const uint64_t da = d0 + (uint64_t)(blk(i, c) >> 4);
 #pragma unroll
                                 for (int j = 0; j < S; j++) {
                                     const int cb = i + j;
                                     if (cb < c0 || cb >= c1) continue;
-                                    const uint64_t db = tc::smem_desc(base + blk(j, c), 128, 256);
+                                    const uint64_t db = d0 + (uint64_t)(blk(j, c) >> 4);
                                     const bool fresh = b == 0 && c == 0 && i == max(0, cb - (S - 1));
                                     tc::mma(tmem + 64u * (uint32_t)(cb - c0), da, db, idesc, fresh ? 0u : 1u);
                                 }
@@ -369,11 +361,8 @@ cudaError_t launch_gram_oz(const void *A, int64_t I, int R, int dtype, double *p
                            long long wait_cycles, int fault_skip, cudaStream_t st) {
     if (R < 1 || R > 64) return cudaErrorInvalidValue;
     const int g = gram_oz_blocks(I);
-    if (dtype == RELATE_F64)
-        return launch_oz<double, 8>((const double *)A, I, R, partial, colexp, err, wait_cycles, fault_skip, g, st);
-    if (dtype == RELATE_F32)
-        return launch_oz<float, 4>((const float *)A, I, R, partial, colexp, err, wait_cycles, fault_skip, g, st);
-    return cudaErrorInvalidValue;
+    if (dtype != RELATE_F64) return cudaErrorInvalidValue;
+    return launch_oz<double, 8>((const double *)A, I, R, partial, colexp, err, wait_cycles, fault_skip, g, st);
 }
 
 }  // namespace relate

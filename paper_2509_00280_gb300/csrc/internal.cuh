@@ -237,14 +237,19 @@ int gram_tc_blocks(int64_t I);
 cudaError_t launch_gram_tc(const __nv_bfloat16 *A, int64_t I, int R, double *partial, int *err,
                            long long wait_cycles, int fault_skip, cudaStream_t st);
 
-// Tensor-core Gram partials for FP64 (8 slices) or FP32 (4 slices) A, R <=
-// 64, any alignment of the element type: k_colexp writes the columns'
-// largest exponent fields to colexp[0..64) (zeroed first), then one FP64
-// upper-triangle partial per block (gram_oz_blocks(I) blocks); err |= 2 and
-// NaN partials if a bounded wait on the tensor cores gave up.
+// Tensor-core Gram partials for FP64 A (exact 7-bit slices), R <= 64, any
+// 8-byte alignment: k_colexp writes the columns' largest exponent fields to
+// colexp[0..64) (zeroed first), then one FP64 upper-triangle partial per
+// block (gram_oz_blocks(I) blocks); err |= 2 and NaN partials if a bounded
+// wait on the tensor cores gave up.
 int gram_oz_blocks(int64_t I);
 cudaError_t launch_gram_oz(const void *A, int64_t I, int R, int dtype, double *partial, int *colexp, int *err,
                            long long wait_cycles, int fault_skip, cudaStream_t st);
+// The same for FP32 A as three BF16 terms per entry (FP32 accumulation per
+// 2048 rows, FP64 beyond), any 4-byte alignment (gram_f32_blocks(I) blocks).
+int gram_f32_blocks(int64_t I);
+cudaError_t launch_gram_f32(const float *A, int64_t I, int R, double *partial, int *err, long long wait_cycles,
+                            int fault_skip, cudaStream_t st);
 
 // V = Hadamard_{k != n} G_k (kept in Vsave); FP64 Cholesky; V^{-1} in FP64
 // (f64_apply) or FP32 (Vinv32, always written).

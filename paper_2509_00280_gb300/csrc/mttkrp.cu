@@ -194,11 +194,18 @@ cudaError_t launch_tile_order(const MttkrpArgs &a_in, int KW, int num_sms, uint1
     if (a.depth >= 1) {
         int64_t g = (int64_t)num_sms * 4;
         if (g > tiles) g = tiles;
+        int bits = mk::kTileBits;  // key width: the row, the level fields, the position
+        for (int s = 0; s <= a.depth; s++) bits += __builtin_popcount(a.rmask[s]);
+        const bool k64 = bits <= 64;
+#define RELATE_TOL(KW_)                                                                            \
+    (k64 ? (mk::k_tile_order_lex<KW_, true><<<(unsigned)g, kThreads, 0, st>>>(a, tperm), 0)        \
+         : (mk::k_tile_order_lex<KW_, false><<<(unsigned)g, kThreads, 0, st>>>(a, tperm), 0))
         switch (KW) {
-        case 1: mk::k_tile_order_lex<1><<<(unsigned)g, kThreads, 0, st>>>(a, tperm); break;
-        case 2: mk::k_tile_order_lex<2><<<(unsigned)g, kThreads, 0, st>>>(a, tperm); break;
-        default: mk::k_tile_order_lex<4><<<(unsigned)g, kThreads, 0, st>>>(a, tperm); break;
+        case 1: RELATE_TOL(1); break;
+        case 2: RELATE_TOL(2); break;
+        default: RELATE_TOL(4); break;
         }
+#undef RELATE_TOL
         return cudaGetLastError();
     }
     int64_t grid = (int64_t)num_sms * 4;

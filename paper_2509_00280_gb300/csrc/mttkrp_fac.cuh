@@ -34,12 +34,14 @@ __device__ __forceinline__ void push_bits(unsigned long long &hi, unsigned long 
 __device__ __forceinline__ int field_width(uint32_t mask) { return __popc(mask); }
 
 // Tile order of a fiber-factored mode: every tile sorted by (i_n, slot 1, ...,
-// slot depth, position in the tile), a bitonic sort of 128-bit keys in shared
-// memory; entries as k_tile_order's (sorted position | (1 + hot slot) << 11).
+// slot depth, position in the tile), a bitonic sort of the concatenated keys
+// in shared memory (64-bit when the fields and the 11 position bits fit, else
+// 128-bit); entries as k_tile_order's (sorted position | (1 + hot slot) << 11).
 // One block per tile, grid-stride.
-template <int KW>
+template <int KW, bool K64>
 __global__ void __launch_bounds__(kThreads) k_tile_order_lex(const MttkrpArgs a, uint16_t *__restrict__ tperm) {
-    __shared__ unsigned long long khi[kTile], klo[kTile];
+    __shared__ unsigned long long klo[kTile];
+    __shared__ unsigned long long khi[K64 ? 1 : kTile];
     __shared__ uint32_t srow[kTile];
     __shared__ uint32_t hkey[kHotHash], hval[kHotHash];
     const int hot_n = a.hot_n, D = a.depth;
@@ -91,8 +93,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_order_lex(const MttkrpArgs a,
                     if (a.rmask[s]) push_bits(hi, lo, fld(w, a.rshift[s], a.rmask[s]), field_width(a.rmask[s]));
                 push_bits(hi, lo, (uint32_t)j, kTileBits);
             }
-            khi[j] = hi;
             klo[j] = lo;
+            if (!K64) khi[j] = hi;
         }
         __syncthreads();
         for (int k = 2; k <= kTile; k <<= 1) {
@@ -100,13 +102,21 @@ __global__ void __launch_bounds__(kThreads) k_tile_order_lex(const MttkrpArgs a,
                 for (int i = threadIdx.x; i < kTile; i += kThreads) {
                     const int ixj = i ^ jj;
                     if (ixj > i) {
-                        const unsigned long long ahi = khi[i], alo = klo[i], bhi = khi[ixj], blo = klo[ixj];
-                        const bool gt = ahi > bhi || (ahi == bhi && alo > blo);
-                        if (gt == ((i & k) == 0)) {
-                            khi[i] = bhi;
-                            klo[i] = blo;
-                            khi[ixj] = ahi;
-                            klo[ixj] = alo;
+                        const unsigned long long alo = klo[i], blo = klo[ixj];
+                        if (K64) {
+                            if ((alo > blo) == ((i & k) == 0)) {
+                                klo[i] = blo;
+                                klo[ixj] = alo;
+                            }
+                        } else {
+                            const unsigned long long ahi = khi[i], bhi = khi[ixj];
+                            const bool gt = ahi > bhi || (ahi == bhi && alo > blo);
+                            if (gt == ((i & k) == 0)) {
+                                khi[i] = bhi;
+                                klo[i] = blo;
+                                khi[ixj] = ahi;
+                                klo[ixj] = alo;
+                            }
                         }
                     }
                 }

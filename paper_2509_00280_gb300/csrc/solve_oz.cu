@@ -191,16 +191,19 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
         for (int h = 0; h < NH; h++) {
             if (tid == 0 && !fault_skip) {
                 tc::fence_after();
-                const uint32_t bm = tc::saddr(sm), bw = tc::saddr(sw) + 1024u * (uint32_t)h;
+                // descriptors differ only in the start address field (address >> 4, below 2^14 for
+                // shared memory): offsets are added to two base descriptors
+                const uint64_t dm0 = tc::smem_desc(tc::saddr(sm), 128, 256);
+                const uint64_t dw0 = tc::smem_desc(tc::saddr(sw) + 1024u * (uint32_t)h, 128, 256);
 #pragma unroll 1
                 for (int c = 0; c < KC; c++)
 #pragma unroll
                     for (int u = 0; u < SO_S; u++) {
-                        const uint64_t da = tc::smem_desc(bm + (uint32_t)((u * 4 + c) * SO_MBLK), 128, 256);
+                        const uint64_t da = dm0 + (uint64_t)(((u * 4 + c) * SO_MBLK) >> 4);
 #pragma unroll
                         for (int v = 0; v < SO_S; v++) {
                             const int g = u + v;
-                            const uint64_t db = tc::smem_desc(bw + (uint32_t)((v * 4 + c) * SO_WBLK), 128, 256);
+                            const uint64_t db = dw0 + (uint64_t)(((v * 4 + c) * SO_WBLK) >> 4);
                             const bool fresh = c == 0 && u == max(0, g - (SO_S - 1));
                             tc::mma(tmem + 32u * (uint32_t)g, da, db, idesc, fresh ? 0u : 1u);
                         }
@@ -225,16 +228,32 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
                 for (int cq = 0; cq < 2; cq++) {  // 8 columns at a time
                     long long w[4][8];  // groups 4k..4k+3 with weights 2^(7 (4k + 3 - g))
 #pragma unroll
-                    for (int k = 0; k < 4; k++)
+                    for (int half8 = 0; half8 < 2; half8++) {  // groups 0..7, then 8..14: two waits
+                        uint32_t va[32], vb[32];
 #pragma unroll
-                        for (int j = 0; j < 8; j++) w[k][j] = 0;
+                        for (int gg = 0; gg < 8; gg++) {
+                            const int g = 8 * half8 + gg;
+                            if (g < SO_GROUPS)
+                                tc::ld8_nowait(tb + 32u * (uint32_t)g + 8u * (uint32_t)cq, (gg < 4 ? va : vb) + 8 * (gg & 3));
+                        }
+                        tc::wait_ld32(va);
+                        tc::wait_ld32(vb);
 #pragma unroll
-                    for (int g = 0; g < SO_GROUPS; g++) {
-                        uint32_t v[8];
-                        tc::ld8(tb + 32u * (uint32_t)g + 8u * (uint32_t)cq, v);
-                        const int k = g >> 2, shg = 7 * (4 * k + 3 - g);
+                        for (int kk = 0; kk < 2; kk++) {
+                            const int k = 2 * half8 + kk;
+                            const uint32_t *v = kk == 0 ? va : vb;
 #pragma unroll
-                        for (int j = 0; j < 8; j++) w[k][j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shg;
+                            for (int j = 0; j < 8; j++) {
+                                long long acc = 0;
+#pragma unroll
+                                for (int gg = 0; gg < 4; gg++) {
+                                    const int g = 4 * k + gg;
+                                    if (g < SO_GROUPS)
+                                        acc += (long long)__float2int_rn(__uint_as_float(v[8 * gg + j])) << (7 * (3 - gg));
+                                }
+                                w[k][j] = acc;
+                            }
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < 8; j++) {

@@ -529,7 +529,7 @@ def main(argv=None):
                     "arrival_rate_req_s": rate if loop == "open" else None, **summ, **q,
                     "nnz_total": sum(r.nnz for r in reqs), "lane_requests": sum(1 for r in reqs if lane and
                                                                                 r.nnz <= args.small_nnz)}
-            fits = {r.rid: r.fit for r in res}
+            fits = {r.rid: (r.fit, r.iters) for r in res}
             all_fits[(form, loop)] = fits
             print(json.dumps(line), flush=True)
             lines.append(line)
@@ -537,8 +537,16 @@ def main(argv=None):
     # every form's fits against the plain FP64 form's (the acceptance bound is 1e-3)
     ref = next((v for (f, _), v in all_fits.items() if f.partition(":")[0] == "f64"), None)
     if ref is not None:
-        diff = {f"{f}/{loop}": float(max(abs(ref[i] - v[i]) for i in v)) for (f, loop), v in all_fits.items()}
+        diff, gap = {}, {}
+        for (f, loop), v in all_fits.items():
+            d = np.array([abs(ref[i][0] - v[i][0]) for i in v])
+            early = np.array([v[i][1] < ref[i][1] for i in v])
+            diff[f"{f}/{loop}"] = float(d.max())
+            gap[f"{f}/{loop}"] = {"p50": float(np.percentile(d, 50)), "p99": float(np.percentile(d, 99)),
+                                  "max": float(d.max()), "over_1e-3": int((d > 1e-3).sum()), "requests": int(d.size),
+                                  "over_1e-3_stopped_earlier": int(((d > 1e-3) & early).sum())}
         print(json.dumps({"max_fit_diff_vs_f64": diff}), flush=True)
+        print(json.dumps({"fit_gap_vs_f64": gap}), flush=True)
     return lines
 
 

@@ -1,17 +1,20 @@
-"""The FP64 / FP32 Gram on the tensor cores (integer slices of every entry,
-exact BF16 products, exact FP32 integer sums per 128-row period).
+"""The Gram on the tensor cores for FP64 inputs (exact integer slices of
+every entry, exact BF16 products, exact FP32 integer sums per 128-row period)
+and FP32 inputs (three BF16 terms per entry, FP32 accumulation per 2048
+rows).
 
 Inputs are k * 2^e with integer k of at most 26 (FP64) or 24 (FP32)
 significant bits and a per-row scale 2^e spread over 31 binades, so that the
 columns are heavy-tailed (a few rows dominate every column, as in the factor
 updates of a Zipf-distributed mode). Every product a_ir a_is is then exact in
 FP64, and math.fsum of the products is the correctly rounded Gram: the
-reference has no error of its own. The bound is the one of the slicing:
-truncation of each entry to 55 (FP64) or 27 (FP32) bits below its column's
-largest exponent, |G_rs - ref| <= 2^-53 sqrt(I) ||A(:, r)|| ||A(:, s)|| for
-FP64 and 2^-25 sqrt(I) ||A(:, r)|| ||A(:, s)|| for FP32 (with a factor 2 of
-slack). A slicing that dropped the low-order pair products would be off by
-about I * 2^-53 on these inputs and fail the larger cases.
+reference has no error of its own. The bounds, relative to
+||A(:, r)|| ||A(:, s)||: FP64, the truncation of each entry 55 bits below its
+column's largest exponent, 2^-53 sqrt(I) (with a factor 2 of slack); a
+slicing that dropped the low-order pair products would be off by about
+I * 2^-53 on these inputs and fail the larger cases. FP32, the dropped terms
+of the three-term split (2^-22) plus FP32 summation over the rows one block
+accumulates before its FP64 drain (at most 2048; worst case linear in them).
 """
 import math
 
@@ -25,7 +28,20 @@ pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 TORCH = {"f64": torch.float64, "f32": torch.float32}
 BITS = {"f64": 26, "f32": 24}
-BOUND = {"f64": 2.0 ** -52, "f32": 2.0 ** -24}
+
+
+def _bound(dt, I):
+    if dt == "f64":
+        return 2.0 * 2.0 ** -53 * math.sqrt(I)
+    # rows one block sums in FP32 before its FP64 drain: the launch takes
+    # min(152, ceil(I / 64)) blocks of ceil(I / blocks) rows
+    blocks = min(152, max(1, -(-I // 64)))
+    return 2.0 ** -22 + min(-(-I // blocks), 2048) * 2.0 ** -24
+
+
+def _norm_err(G, ref):
+    norms = np.sqrt(np.diag(ref))
+    return np.abs(G - ref) / np.maximum(np.outer(norms, norms), 1e-300)
 
 
 def _heavy(I, R, dt, seed):
@@ -61,10 +77,9 @@ def test_sliced_gram_within_the_slicing_bound(dt, I, R):
     A = _heavy(I, R, dt, seed=I * 100 + R)
     ref = _exact_gram(A)
     G = _gpu_gram(A, dt, offset=1 if I % 2 else 0)
-    norms = np.sqrt(np.diag(ref))
-    err = np.abs(G - ref) / np.maximum(np.outer(norms, norms), 1e-300)
+    err = _norm_err(G, ref)
     assert np.isfinite(G).all()
-    assert err.max() <= 2.0 * BOUND[dt] * math.sqrt(I), (dt, I, R, err.max())
+    assert err.max() <= _bound(dt, I), (dt, I, R, err.max())
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
@@ -75,7 +90,7 @@ def test_sliced_gram_zero_and_nonfinite_columns(dt):
     assert np.all(G[3, :] == 0.0) and np.all(G[:, 3] == 0.0)
     ok = [c for c in range(16) if c != 3]
     ref = _exact_gram(A)
-    assert np.allclose(G[np.ix_(ok, ok)], ref[np.ix_(ok, ok)], rtol=1e-12 if dt == "f64" else 1e-5, atol=0)
+    assert _norm_err(G[np.ix_(ok, ok)], ref[np.ix_(ok, ok)]).max() <= _bound(dt, 3000)
     A[17, 5] = np.inf
     G = _gpu_gram(A, dt)
     assert np.isnan(G[5, :]).all() and np.isnan(G[:, 5]).all()
