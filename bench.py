@@ -52,11 +52,11 @@ NUM_SMS = 152
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": "b5bd63573afc8791af38b7c0c8b1ac06fe4c6285dfc65b50f93e284c2ed40a9b",
+NCU_TRAFFIC = {"sha256": "1bb54f54a7d88b13dab5c6586d0d00386a72b7108903cba587af786ed68f96b5",
                # full-size 1-pass capture (dram__bytes_read.sum + dram__bytes_write.sum)
-               # of the 4 per-mode launches of the FP64 factored MTTKRP: 19.94 / 18.51
-               # / 17.36 / 16.21 GB, their mean
-               "bytes_per_launch": 18.0e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
+               # of the 4 per-mode launches of the FP64 factored MTTKRP: 19.93 / 18.34
+               # / 17.28 / 16.16 GB, their mean
+               "bytes_per_launch": 17.93e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
 
 
 def _peaks():

@@ -29,6 +29,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "slices.cuh"
 #include "tcgen05.cuh"
 
 namespace relate {
@@ -42,26 +43,13 @@ constexpr int OZ_BLOCKS = 152;
 constexpr int OZ_ITEMS = OZ_STAGE_ROWS / 2 * 64 / OZ_THREADS;  // (column, row pair) items per thread per stage
 
 // two stages of slices, then the FP64 accumulators [half][column][row]
-template <int S> constexpr size_t oz_smem_bytes() { return 2 * (size_t)S * OZ_CHUNKS * OZ_BLK + 2 * 64 * 64 * 8; }
-
-// Exponent field of an entry as an FP64 number (0: zero or subnormal,
-// 0x7ff: Inf or NaN), its 53-bit significand and its sign.
-template <typename T> struct OzBits;
-template <> struct OzBits<double> {
-    __device__ static int expo(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
-    __device__ static void split(double x, uint64_t &mant, int &e, uint32_t &neg) {
-        const uint64_t b = (uint64_t)__double_as_longlong(x);
-        e = (int)((b >> 52) & 0x7ff);
-        neg = (uint32_t)(b >> 63);
-        mant = (b & 0xfffffffffffffull) | (1ull << 52);
-    }
-};
+// two stages of slices, then four 64-bit integer words per pair (r <= s) of the block's sums
+template <int S> constexpr size_t oz_smem_bytes() { return 2 * (size_t)S * OZ_CHUNKS * OZ_BLK + 4 * 2080 * 8; }
 
 // Largest exponent field per column of a row-major I x R matrix (R <= 64),
 // atomicMax into colexp[0..R) (zeroed by the launcher). A warp walks rows,
 // lane l holding columns l and l + 32; 8 rows per step are in flight.
-template <typename T>
-__global__ void __launch_bounds__(256) k_colexp(const T *__restrict__ A, int64_t I, int R, int *__restrict__ colexp) {
+__global__ void __launch_bounds__(256) k_colexp(const double *__restrict__ A, int64_t I, int R, int *__restrict__ colexp) {
     __shared__ int smax[64];
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 64) smax[threadIdx.x] = 0;
@@ -71,17 +59,17 @@ __global__ void __launch_bounds__(256) k_colexp(const T *__restrict__ A, int64_t
     int m0 = 0, m1 = 0;
     const bool c0 = lane < R, c1 = lane + 32 < R;
     for (int64_t i = w0; i < I; i += 8 * nw) {
-        T x0[8], x1[8];
+        double x0[8], x1[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
             const int64_t row = i + u * nw;
-            x0[u] = (row < I && c0) ? A[row * R + lane] : T(0);
-            x1[u] = (row < I && c1) ? A[row * R + lane + 32] : T(0);
+            x0[u] = (row < I && c0) ? A[row * R + lane] : 0.0;
+            x1[u] = (row < I && c1) ? A[row * R + lane + 32] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 8; u++) {
-            m0 = max(m0, OzBits<T>::expo(x0[u]));
-            m1 = max(m1, OzBits<T>::expo(x1[u]));
+            m0 = max(m0, sl::expo_of(x0[u]));
+            m1 = max(m1, sl::expo_of(x1[u]));
         }
     }
     atomicMax(&smax[lane], m0);
@@ -90,34 +78,16 @@ __global__ void __launch_bounds__(256) k_colexp(const T *__restrict__ A, int64_t
     if (threadIdx.x < R && smax[threadIdx.x] > 0) atomicMax(colexp + threadIdx.x, smax[threadIdx.x]);
 }
 
-// The S slices of one entry as BF16 bit patterns (sign on every slice).
-template <int S>
-__device__ __forceinline__ void oz_slices(uint64_t mant, int e, int E, uint32_t neg, uint32_t (&u)[S]) {
-    uint64_t q = 0;
-    if (e != 0) {
-        const int sh = max(E - e - 2, -2);  // e <= E: |q| < 2^55
-        q = sh >= 0 ? (sh < 64 ? mant >> sh : 0ull) : mant << (-sh);
-    }
-    const uint32_t sg = neg << 15;
-#pragma unroll
-    for (int k = 0; k < S; k++) {
-        const uint32_t d = (uint32_t)(q >> (7 * (7 - k))) & 127u;
-        // d as an FP32 value (exact: 2^23 + d - 2^23), whose top 16 bits are its BF16 pattern
-        const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
-        u[k] = (__float_as_uint(f) >> 16) | sg;
-    }
-}
-
-// Drain of the tensor-memory blocks [C0, C1) of one pass into this thread's
-// FP64 accumulators: block c holds group g = c + OFF (OFF = 0 in the lower
-// 64 lanes, S / 2 in the upper 64). Each FP32 value is an exact integer; the
-// groups are combined exactly in 64-bit words of four groups, word k
-// weighing 2^(7 (11 - 4k)), so q_r q_s = sum_g acc_g 2^(7 (14 - g)).
-// acc points at this thread's row of [column][row] FP64 accumulators.
+// Drain of the tensor-memory blocks [C0, C1) of one pass: block c holds
+// group g = c + OFF (OFF = 0 in the lower 64 lanes, S / 2 in the upper 64).
+// Each FP32 value is an exact integer; the groups are combined exactly in
+// 64-bit words of four groups (word k = sum_{g = 4k..4k+3} acc_g
+// 2^(7 (4k + 3 - g)), so q_r q_s = sum_k word_k 2^(7 (11 - 4k))) and added
+// with 64-bit shared-memory atomics to the block's words of the pair (r, s),
+// pair index p = r R - r (r - 1) / 2 + s - r, for r <= s < R (both halves of
+// the lanes add to the same pairs). No FP64 arithmetic until the end.
 template <int OFF, int C0, int C1>
-__device__ __forceinline__ void oz_drain(uint32_t tbase, double *acc) {
-    constexpr double kWordWeight[4] = {1.5111572745182865e23 /* 2^77 */, 562949953421312.0 /* 2^49 */,
-                                       2097152.0 /* 2^21 */, 0.0078125 /* 2^-7 */};
+__device__ __forceinline__ void oz_drain(uint32_t tbase, unsigned long long *words, int npairs, int r, int s0, int R) {
 #pragma unroll
     for (int qc = 0; qc < 4; qc++) {  // 8 columns at a time, all blocks of the pass in flight
         uint32_t va[32], vb[32];
@@ -140,11 +110,13 @@ __device__ __forceinline__ void oz_drain(uint32_t tbase, double *acc) {
         }
 #pragma unroll
         for (int j = 0; j < 8; j++) {
-            double d = 0.0;
+            const int s = s0 + 8 * qc + j;
+            if (s < r || s >= R) continue;
+            const int p = r * R - r * (r - 1) / 2 + (s - r);
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                if ((C0 + OFF) >> 2 <= k && k <= (C1 - 1 + OFF) >> 2) d = fma((double)w[k][j], kWordWeight[k], d);
-            acc[64 * (8 * qc + j)] += d;
+                if ((C0 + OFF) >> 2 <= k && k <= (C1 - 1 + OFF) >> 2)
+                    atomicAdd(words + (size_t)k * npairs + p, (unsigned long long)w[k][j]);
         }
     }
 }
@@ -165,7 +137,7 @@ template <typename T, int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_gram_oz(const T *__restrict__ A, int64_t I, int R, const int *__restrict__ colexp, double *__restrict__ partial,
               int *__restrict__ err, long long wait_cycles, int fault_skip) {
-    static_assert(S == 4 || S == 8, "4 or 8 slices");
+    static_assert(S == 8, "8 slices: q exactly");
     constexpr int H = S / 2;
     constexpr int NCB = 3 * H - 1;                   // tensor-memory blocks of one period
     constexpr int PA = NCB < 8 ? NCB : 8;            // blocks of the first pass
@@ -176,7 +148,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __shared__ uint32_t tmem_base;
     __shared__ int gave_up;
     __shared__ int sE[64];
-    double *acc_s = reinterpret_cast<double *>(smem_oz + 2 * (size_t)STAGE_BYTES);  // [half][column][row]
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(smem_oz + 2 * (size_t)STAGE_BYTES);  // [k][pair]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int npairs = R * (R + 1) / 2;
 
@@ -186,7 +158,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int nper = (int)((r1 - r0 + 2 * OZ_STAGE_ROWS - 1) / (2 * OZ_STAGE_ROWS));
 
     if (tid < 64) sE[tid] = tid < R ? colexp[tid] : 0;
-    for (int i = tid; i < 2 * 64 * 64; i += OZ_THREADS) acc_s[i] = 0.0;
+    for (int i = tid; i < 4 * npairs; i += OZ_THREADS) words[i] = 0ull;
     if (warp == 0) tc::alloc(&tmem_base, TMEM_COLS);
     if (tid == 0) {
         tc::mbar_init1(&bar);
@@ -206,7 +178,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const bool upper = q >= 2;
     const bool drainer = ((q & 1) == 0 && (hcol == 0 || R > 32)) || ((q & 1) == 1 && hcol == 1 && R > 32);
     const int rloc = 32 * (q & 1) + lane;
-    double *acc = acc_s + (upper ? 64 * 64 : 0) + 64 * (32 * hcol) + rloc;  // column s at acc[64 * (s - 32h)]
     const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * hcol);
 
     // this thread's staging items: column m, row pairs kp of a stage
@@ -240,14 +211,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     const int c = kp >> 3;
                     const uint32_t off =
                         (uint32_t)((m >> 3) * 256 + ((kp & 7) >> 2) * 128 + (m & 7) * 16 + (kp & 3) * 4);
-                    uint32_t u0[S], u1[S];
-                    uint64_t mant;
-                    int e;
-                    uint32_t neg;
-                    OzBits<T>::split(x[iu][0], mant, e, neg);
-                    oz_slices<S>(mant, e, Em, neg, u0);
-                    OzBits<T>::split(x[iu][1], mant, e, neg);
-                    oz_slices<S>(mant, e, Em, neg, u1);
+                    uint32_t u0[8], u1[8];
+                    sl::slices8((double)x[iu][0], Em, u0);
+                    sl::slices8((double)x[iu][1], Em, u1);
 #pragma unroll
                     for (int k = 0; k < S; k++)
                         *reinterpret_cast<uint32_t *>(buf + blk(k, c) + off) = u0[k] | (u1[k] << 16);
@@ -294,11 +260,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tc::fence_after();
             if (drainer) {
                 if (pass == 0) {
-                    if (upper) oz_drain<H, 0, PA>(tbase, acc);
-                    else oz_drain<0, 0, PA>(tbase, acc);
+                    if (upper) oz_drain<H, 0, PA>(tbase, words, npairs, rloc, 32 * hcol, R);
+                    else oz_drain<0, 0, PA>(tbase, words, npairs, rloc, 32 * hcol, R);
                 } else if constexpr (NCB > 8) {
-                    if (upper) oz_drain<H, 8, NCB>(tbase, acc);
-                    else oz_drain<0, 8, NCB>(tbase, acc);
+                    if (upper) oz_drain<H, 8, NCB>(tbase, words, npairs, rloc, 32 * hcol, R);
+                    else oz_drain<0, 8, NCB>(tbase, words, npairs, rloc, 32 * hcol, R);
                 }
             }
             tc::fence_before();
@@ -324,7 +290,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             double g;
             if (Er >= 0x7ff || Es >= 0x7ff) g = __longlong_as_double(0x7ff8000000000000ll);
             else if (Er == 0 || Es == 0) g = 0.0;
-            else g = ldexp(acc_s[64 * s2 + r] + acc_s[64 * 64 + 64 * s2 + r], Er + Es - 2154);
+            else {
+                // q_r q_s = sum_k word_k 2^(7 (11 - 4k)): the words exactly in FP64 (|word| < 2^63
+                // rounds once each), summed from the smallest weight up
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 3; k >= 0; k--)
+                    acc += ldexp((double)(long long)words[(size_t)k * npairs + pp], 7 * (11 - 4 * k));
+                g = ldexp(acc, Er + Es - 2154);
+            }
             partial[(int64_t)blockIdx.x * npairs + pp] = g;
         }
     }
@@ -340,7 +314,7 @@ cudaError_t launch_oz(const T *A, int64_t I, int R, double *partial, int *colexp
     if (e != cudaSuccess) return e;
     int64_t gw = (I + 8 * 8 - 1) / (8 * 8);  // 8 warps per block, 8 rows in flight per warp
     const int g1 = (int)(gw > 152 * 4 ? 152 * 4 : gw < 1 ? 1 : gw);
-    k_colexp<T><<<g1, 256, 0, st>>>(A, I, R, colexp);
+    k_colexp<<<g1, 256, 0, st>>>(A, I, R, colexp);
     auto kern = k_gram_oz<T, S>;
     if ((e = allow_max_dynamic_smem(kern)) != cudaSuccess) return e;
     kern<<<g, OZ_THREADS, oz_smem_bytes<S>(), st>>>(A, I, R, colexp, partial, err,

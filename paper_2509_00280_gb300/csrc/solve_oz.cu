@@ -30,10 +30,14 @@
 // accumulators (480 tensor-memory columns) and 8 warps drain them. The tile
 // is read completely before its rows are overwritten (in place).
 #include "internal.cuh"
+#include "slices.cuh"
 #include "tcgen05.cuh"
 
 namespace relate {
 namespace {
+
+using sl::expo_of;
+using sl::slices8;
 
 constexpr int SO_THREADS = 256;
 constexpr int SO_ROWS = 128;
@@ -45,28 +49,6 @@ constexpr int SO_MBYTES = SO_S * 4 * SO_MBLK;     // 128 KB
 constexpr int SO_WBYTES = SO_S * 4 * SO_WBLK;     // 64 KB
 constexpr int SO_BLOCKS = 152;
 constexpr uint32_t SO_TMEM_COLS = 512;
-
-__device__ __forceinline__ int expo_of(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
-
-// BF16 pattern of the signed 7-bit slice k (0 = most significant) of x on
-// the scale of exponent field E (E >= the field of x).
-__device__ __forceinline__ void slices8(double x, int E, uint16_t (&u)[SO_S]) {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff);
-    uint64_t q = 0;
-    if (e != 0) {
-        const uint64_t mant = (b & 0xfffffffffffffull) | (1ull << 52);
-        const int sh = max(E - e - 2, -2);
-        q = sh >= 0 ? (sh < 64 ? mant >> sh : 0ull) : mant << (-sh);
-    }
-    const uint32_t sg = (uint32_t)(b >> 63) << 15;
-#pragma unroll
-    for (int k = 0; k < SO_S; k++) {
-        const uint32_t d = (uint32_t)(q >> (7 * (7 - k))) & 127u;
-        const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;  // d exactly, as FP32
-        u[k] = (uint16_t)((__float_as_uint(f) >> 16) | sg);
-    }
-}
 
 // Round a signed 128-bit integer times 2^scale to the nearest FP64 (ties to
 // even), integer operations only while the result is a normal number.
@@ -127,13 +109,13 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
     __syncthreads();
     for (int x = tid; x < 64 * 64; x += SO_THREADS) {  // (n = s, k = r), zero outside R x R
         const int s = x >> 6, r = x & 63;
-        uint16_t u[SO_S];
+        uint32_t u[SO_S];
         const double w = (s < R && r < R) ? W[r * R + s] : 0.0;
         slices8(w, s < R ? wexp[s] : 0, u);
         const uint32_t off = (uint32_t)((s >> 3) * 256 + ((r & 15) >> 3) * 128 + (s & 7) * 16 + (r & 7) * 2);
 #pragma unroll
         for (int k = 0; k < SO_S; k++)
-            *reinterpret_cast<uint16_t *>(sw + (size_t)(k * 4 + (r >> 4)) * SO_WBLK + off) = u[k];
+            *reinterpret_cast<uint16_t *>(sw + (size_t)(k * 4 + (r >> 4)) * SO_WBLK + off) = (uint16_t)u[k];
     }
     if (warp == 0) tc::alloc(&tmem_base, SO_TMEM_COLS);
     if (tid == 0) {
@@ -170,17 +152,17 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
 #pragma unroll
             for (int g8 = 0; g8 < 4; g8++) {  // 8 consecutive K entries = one 16-byte core-matrix row
                 const int r0 = sc0 + 8 * g8;
-                uint16_t u[8][SO_S];
+                uint32_t u[8][SO_S];
 #pragma unroll
                 for (int j = 0; j < 8; j++) slices8(x[8 * g8 + j], e, u[j]);
                 const uint32_t off = (uint32_t)((si >> 3) * 256 + ((r0 & 15) >> 3) * 128 + (si & 7) * 16);
 #pragma unroll
                 for (int k = 0; k < SO_S; k++) {
                     uint4 v;
-                    v.x = (uint32_t)u[0][k] | ((uint32_t)u[1][k] << 16);
-                    v.y = (uint32_t)u[2][k] | ((uint32_t)u[3][k] << 16);
-                    v.z = (uint32_t)u[4][k] | ((uint32_t)u[5][k] << 16);
-                    v.w = (uint32_t)u[6][k] | ((uint32_t)u[7][k] << 16);
+                    v.x = u[0][k] | (u[1][k] << 16);
+                    v.y = u[2][k] | (u[3][k] << 16);
+                    v.z = u[4][k] | (u[5][k] << 16);
+                    v.w = u[6][k] | (u[7][k] << 16);
                     *reinterpret_cast<uint4 *>(sm + (size_t)(k * 4 + (r0 >> 4)) * SO_MBLK + off) = v;
                 }
             }
@@ -243,16 +225,10 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
                             const int k = 2 * half8 + kk;
                             const uint32_t *v = kk == 0 ? va : vb;
 #pragma unroll
-                            for (int j = 0; j < 8; j++) {
-                                long long acc = 0;
-#pragma unroll
-                                for (int gg = 0; gg < 4; gg++) {
-                                    const int g = 4 * k + gg;
-                                    if (g < SO_GROUPS)
-                                        acc += (long long)__float2int_rn(__uint_as_float(v[8 * gg + j])) << (7 * (3 - gg));
-                                }
-                                w[k][j] = acc;
-                            }
+                            for (int j = 0; j < 8; j++)  // group 15 does not exist: its slot reads as 0
+                                w[k][j] = sl::word4(__uint_as_float(v[j]), __uint_as_float(v[8 + j]),
+                                                    __uint_as_float(v[16 + j]),
+                                                    4 * k + 3 < SO_GROUPS ? __uint_as_float(v[24 + j]) : 0.0f);
                         }
                     }
 #pragma unroll

@@ -214,7 +214,8 @@ class Server:
 
     def __init__(self, workers: int = 8, budget_bytes: int | None = None, device: int = 0,
                  use_graph: bool = True, max_bypass: int = 8, small_nnz: int = 0, batch_max: int = 16,
-                 chunk_iters: int = 5, small_budget_frac: float = 0.1, small_tol: float = 1e-4):
+                 chunk_iters: int = 5, small_budget_frac: float = 0.1, small_tol: float = 1e-4,
+                 tune_nnz: int = 0):
         import torch
         self._torch = torch
         if not torch.cuda.is_available():
@@ -236,6 +237,7 @@ class Server:
         self.batch_max = int(batch_max)
         self.chunk_iters = int(chunk_iters)
         self.small_tol = float(small_tol)  # the lane's stopping tolerance (one per lockstep call)
+        self.tune_nnz = int(tune_nnz)  # requests this large get their kernel plans tuned first (0: never)
         self._t0 = time.perf_counter()
         self._threads = []
         self._errors = []
@@ -311,6 +313,12 @@ class Server:
             factors = initial_factors(req.dims, req.R, req.init_seed, self.device, tdt)
         h = rl.relate_encode(req.coords, req.vals, req.dims, factor_dtype=req.precision, stream=stream)
         try:
+            if self.tune_nnz > 0 and req.nnz >= self.tune_nnz:
+                # the per-mode plan search of tune.py, timed on this worker's
+                # stream (one launch per plan, no L2 flush); the handle keeps
+                # the fastest plans for its CP-ALS
+                from .tune import tune_modes
+                tune_modes(h, req.dims, req.R, req.precision, factors, reps=1, stream=stream, flush_l2=False)
             if self.use_graph:
                 rl.relate_set_cpals_graph(h, True)
             out = rl.relate_cpals(h, req.R, req.max_iters, req.tol, factors)
@@ -421,13 +429,15 @@ def summarize(results, makespan: float) -> dict:
 
 def run_mix(requests, arrivals=None, workers: int = 8, budget_bytes: int | None = None,
             use_graph: bool = True, small_nnz: int = 0, batch_max: int = 16, chunk_iters: int = 5,
-            small_tol: float = 1e-4):
+            small_tol: float = 1e-4, tune_nnz: int = 0):
     """Serves `requests` (Request objects). arrivals: None = closed loop (all
     submitted at t = 0), else the arrival time of each request in seconds.
     small_nnz > 0 routes requests of at most that many nonzeros to the batch
-    lane. Returns (results in request order, summary dict, queue statistics)."""
+    lane; tune_nnz > 0 tunes the kernel plans of requests of at least that
+    many nonzeros. Returns (results in request order, summary dict, queue
+    statistics)."""
     srv = Server(workers=workers, budget_bytes=budget_bytes, use_graph=use_graph, small_nnz=small_nnz,
-                 batch_max=batch_max, chunk_iters=chunk_iters, small_tol=small_tol)
+                 batch_max=batch_max, chunk_iters=chunk_iters, small_tol=small_tol, tune_nnz=tune_nnz)
     futs = []
     t0 = srv.now()
     try:
@@ -474,8 +484,10 @@ def main(argv=None):
     """Serves the request mix in several forms: the first form closed loop
     measures the service rate S, then every form serves Poisson arrivals at
     0.8 S (and, with --closed-all, also closed loop). A form is
-    "precision[:lane]": factor precision, and ":lane" sends requests of at most
-    --small-nnz nonzeros to the batch lane. Prints one JSON line per run."""
+    "precision[:lane][:tuned]": factor precision; ":lane" sends requests of at
+    most --small-nnz nonzeros to the batch lane; ":tuned" tunes the kernel
+    plans (tune.tune_modes) of requests of at least --tune-nnz nonzeros
+    before their CP-ALS. Prints one JSON line per run."""
     import argparse
     import json
     import os
@@ -495,6 +507,7 @@ def main(argv=None):
     ap.add_argument("--small-nnz", type=int, default=200_000)
     ap.add_argument("--batch-max", type=int, default=16)
     ap.add_argument("--chunk-iters", type=int, default=5)
+    ap.add_argument("--tune-nnz", type=int, default=2_000_000)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-open-loop", action="store_true")
     ap.add_argument("--closed-all", action="store_true", help="closed loop for every form, not only the first")
@@ -510,8 +523,9 @@ def main(argv=None):
     print(json.dumps({"generated": len(mix), "nnz_total": sum(r.nnz for r in mix), "generation_s": gen_s}),
           flush=True)
     for k, form in enumerate(forms):
-        prec, _, opt = form.partition(":")
-        lane = opt == "lane"
+        prec, *opts = form.split(":")
+        lane = "lane" in opts
+        tuned = "tuned" in opts
         reqs = with_precision(mix, prec)
         loops = ["closed", "open"] if (k == 0 or args.closed_all) else ["open"]
         for loop in loops:
@@ -521,10 +535,12 @@ def main(argv=None):
             res, summ, q = run_mix(reqs, arr, workers=args.workers, budget_bytes=budget,
                                    use_graph=not args.no_graph, small_nnz=args.small_nnz if lane else 0,
                                    batch_max=args.batch_max, chunk_iters=args.chunk_iters,
-                                   small_tol=reqs[0].tol if reqs else 1e-4)
+                                   small_tol=reqs[0].tol if reqs else 1e-4,
+                                   tune_nnz=args.tune_nnz if tuned else 0)
             if loop == "closed" and rate is None:
                 rate = 0.8 * summ["throughput_req_s"]
-            line = {"serve": prec, "lane": lane, "small_nnz": args.small_nnz if lane else 0, "loop": loop,
+            line = {"serve": prec, "lane": lane, "small_nnz": args.small_nnz if lane else 0,
+                    "tune_nnz": args.tune_nnz if tuned else 0, "loop": loop,
                     "workers": args.workers, "graph": not args.no_graph,
                     "arrival_rate_req_s": rate if loop == "open" else None, **summ, **q,
                     "nnz_total": sum(r.nnz for r in reqs), "lane_requests": sum(1 for r in reqs if lane and

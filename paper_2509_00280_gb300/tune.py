@@ -308,32 +308,39 @@ def apply_config(rl, h, mode: int, cfg: ModeConfig) -> None:
                             list(cfg.level) if cfg.level is not None else None, cfg.col_passes)
 
 
-def tune_modes(h, dims, R: int, factor_dtype: str, factors, reps: int = 3, verbose: bool = False):
+def tune_modes(h, dims, R: int, factor_dtype: str, factors, reps: int = 3, verbose: bool = False, stream=None,
+               flush_l2: bool = True):
     """Per mode, times every plan of mode_configs on the encoded tensor (CUDA
-    events, L2 flushed between launches) and keeps the fastest; the handle is
-    left with the chosen plans. Returns [(ModeConfig, seconds, AUTO seconds)]."""
+    events on `stream`, default the current stream; L2 flushed between
+    launches unless flush_l2 is False) and keeps the fastest; the handle is
+    left with the chosen plans. Only `stream` is synchronised, so a serving
+    worker can tune while other streams run. Returns [(ModeConfig, seconds,
+    AUTO seconds)]."""
     import torch
 
     from . import relate as rl
 
     dev = factors[0].device
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
     acc = torch.float64 if factor_dtype == "f64" else torch.float32
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if flush_l2 else None
     chosen = []
     for n in range(len(dims)):
         out = torch.empty((int(dims[n]), R), dtype=acc, device=dev)
 
         def time_mode():
             ts = []
-            for r in range(reps + 1):
-                flush.fill_(float(r))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                rl.relate_mttkrp(h, n, factors, R, out)
-                e1.record()
-                torch.cuda.synchronize()
-                if r:
-                    ts.append(e0.elapsed_time(e1) / 1e3)
+            with torch.cuda.stream(st):
+                for r in range(reps + 1):
+                    if flush is not None:
+                        flush.fill_(float(r))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    rl.relate_mttkrp(h, n, factors, R, out, st)
+                    e1.record(st)
+                    st.synchronize()
+                    if r:
+                        ts.append(e0.elapsed_time(e1) / 1e3)
             return float(np.median(ts))
 
         rl.relate_set_conflict(h, n, 0)

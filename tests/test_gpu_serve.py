@@ -6,6 +6,7 @@
 * a served request matches the CPU oracle's CP-ALS from the same initial
   factors (FP64 within 1e-9, FP32 fit within 1e-3);
 * admission keeps the admitted footprint within a small budget;
+* requests whose kernel plans are tuned first give the same models;
 * the batch lane (small requests in lockstep, one persistent MTTKRP launch
   per mode for all of them) gives each request the same CP model alone, in a
   mix larger than one batch, and through the worker path.
@@ -135,3 +136,15 @@ def test_batch_lane_matches_the_worker_path_and_the_oracle():
                 for f in serve.initial_factors(r.dims, r.R, r.init_seed, DEV, torch.float32)]
         ref = oracle.cpals(r.coords, r.vals, r.dims, r.R, 6, 0.0, init)
         assert np.max(np.abs(a.fit_trace - ref["fit_trace"])) <= 1e-9
+
+
+def test_tuned_plans_give_the_same_models():
+    """Requests whose kernel plans are tuned before their CP-ALS (tune_nnz)
+    converge to the same models as with the AUTO plans: the plans change the
+    kernels' association of the sums, not the method (FP64: within 1e-9)."""
+    reqs = serve.with_precision(_mix(6, nnz_range=(5e4, 3e5)), "f64")
+    auto, _, _ = serve.run_mix(reqs, workers=3)
+    tuned, _, _ = serve.run_mix(reqs, workers=3, tune_nnz=1)
+    for a, b in zip(auto, tuned):
+        assert a.status == 0 and b.status == 0
+        assert abs(a.fit - b.fit) <= 1e-9, (a.rid, a.fit, b.fit)
