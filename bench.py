@@ -59,6 +59,35 @@ NCU_TRAFFIC = {"sha256": "1bb54f54a7d88b13dab5c6586d0d00386a72b7108903cba587af78
                "bytes_per_launch": 17.93e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
 
 
+# L1 / L2 traffic of the MTTKRP kernels from ncu captures of smaller cases of
+# the same workload families (l1tex__t_bytes.sum and lts__t_bytes.sum, mean
+# per launch over the modes), scaled to a launch of the timed workload by its
+# nonzero count: the cache traffic of a launch is proportional to its
+# nonzeros. Filled from profiles/k_mttkrp_cache_traffic.md.
+_SHA_CACHE = "1bb54f54a7d88b13dab5c6586d0d00386a72b7108903cba587af786ed68f96b5"
+NCU_CACHE = [
+    {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "f64", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
+     "nnz": 30e6, "l1_bytes": 4.455e10, "l2_bytes": 3.724e10},
+    {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "f32", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
+     "nnz": 30e6, "l1_bytes": 2.413e10, "l2_bytes": 1.424e10},
+    {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "bf16", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
+     "nnz": 30e6, "l1_bytes": 1.280e10, "l2_bytes": 7.761e9},
+    {"sha256": _SHA_CACHE, "family": "zipf3d-200Kx200Kx5K", "dtype": "f32", "workload": "zipf3d-200Kx200Kx5K-20M",
+     "nnz": 20e6, "l1_bytes": 5.255e9, "l2_bytes": 2.006e9},
+]
+
+
+def _cache_rates(fdt, workload, nnz, sec_per_launch):
+    family = workload.rsplit("-", 1)[0]
+    for c in NCU_CACHE:
+        if c["sha256"] == _kernel_sha() and c["family"] == family and c["dtype"] == fdt:
+            scale = nnz / c["nnz"]
+            return {"l1_gbs": c["l1_bytes"] * scale / sec_per_launch / 1e9,
+                    "l2_gbs": c["l2_bytes"] * scale / sec_per_launch / 1e9,
+                    "source": f"ncu l1tex__t_bytes.sum / lts__t_bytes.sum of {c['workload']}, scaled to {int(nnz)} nonzeros"}
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -347,7 +376,7 @@ def _time_kernels(rl, torch, h, stream, d_fac, spec, R, fdt, dev, reps):
     return stats, per_mode
 
 
-def _roofline(per_mode, fdt, workload):
+def _roofline(per_mode, fdt, workload, nnz=None):
     """Roofline of the MTTKRP kernel over all modes: FP64 factors are bound by
     the FP64 pipe (flops = nnz * R * N per launch against the FP64 peak), FP32
     and BF16 factors against the measured HBM copy bandwidth (algorithmic
@@ -361,14 +390,15 @@ def _roofline(per_mode, fdt, workload):
     if NCU_TRAFFIC["sha256"] == _kernel_sha() and NCU_TRAFFIC["workload"] == workload and \
             NCU_TRAFFIC.get("dtype", "f32") == fdt:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
+    cache = _cache_rates(fdt, workload, nnz, ms_total / 1000.0 / N) if nnz else None
     if fdt == "f64":
         tf = sum(m["alg_flops"] for m in per_mode) / (ms_total / 1000.0) / 1e12
         peak = _fp64_peak_tflops()
         return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
                 "traffic": traffic, "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flops x max SM clock",
-                "kernel": "k_mttkrp_fac", "hbm": hbm, "per_mode": per_mode}
+                "kernel": "k_mttkrp_fac", "hbm": hbm, "cache": cache, "per_mode": per_mode}
     return {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": gbs / peak_hbm,
-            "traffic": traffic, "peak_kind": kind, "kernel": "k_mttkrp", "per_mode": per_mode}
+            "traffic": traffic, "peak_kind": kind, "kernel": "k_mttkrp", "cache": cache, "per_mode": per_mode}
 
 
 def _time_dense(rl, torch, dev, I, R, fdt, reps):
@@ -547,7 +577,7 @@ def main():
     h = rl.relate_encode(d_coords, d_vals, spec.dims, factor_dtype=fdt, stream=stream)
     stats, per_mode = _time_kernels(rl, torch, h, stream, d_fac, spec, R, fdt, dev, 5)
     h.close()
-    roof = _roofline(per_mode, fdt, spec.name)
+    roof = _roofline(per_mode, fdt, spec.name, spec.nnz)
 
     # --- e2e through the C ABI with host buffers
     pin_c = torch.from_numpy(coords).pin_memory()
@@ -609,7 +639,7 @@ def main():
         hv.close()
         var_out[vdt] = {"value": units_step * vsteps * world / (vms / 1000.0), "unit": UNIT,
                         "ms_per_step": vms / vsteps, "steps": vsteps, "dtype": "f32",
-                        "final_fit": vres["fit"], "roofline": _roofline(vper, vdt, spec.name)}
+                        "final_fit": vres["fit"], "roofline": _roofline(vper, vdt, spec.name, spec.nnz)}
         del vc, vv, vinit, vfac
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
