@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(kThreads, FacCfg<NT, FT>::MinBlocks) k_mttkrp_
     constexpr int NI = NT;
     constexpr int U = FacCfg<NT, FT>::U;  // records in flight per group
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int next_chunk;       // the next unclaimed chunk of the tile (G = 32)
+    constexpr int kChunk = 64;       // records per claimed chunk
 
     const int G = 1 << log2G;
     const int lane = threadIdx.x & 31;
@@ -254,20 +256,22 @@ __global__ void __launch_bounds__(kThreads, FacCfg<NT, FT>::MinBlocks) k_mttkrp_
             }
             rend[p] = (uint8_t)e;
         }
+        if (threadIdx.x == 0) next_chunk = 0;
         __syncthreads();
 
-        // ---- slices: contiguous record ranges per group, boundaries moved
-        // forward to the next change of output row (at most kSnap records)
-        const int chunk = (nt + ngroups - 1) / ngroups;
-        auto snap = [&](int x) -> int {
-            if (x <= 0 || x >= nt || chunk < kSnap) return min(max(x, 0), nt);
+        // ---- slices: contiguous record ranges, boundaries moved forward to
+        // the next change of output row (at most kSnap records). A group of a
+        // whole warp (G = 32) takes kChunk-record chunks from a shared counter
+        // until the tile is done, so that warps whose records close more
+        // fibers (more FP64 work) do not hold the others at the tile's end;
+        // narrower groups take one equal slice each.
+        auto snap_to = [&](int x, int ch) -> int {
+            if (x <= 0 || x >= nt || ch < kSnap) return min(max(x, 0), nt);
             for (int y = x - 1; y < nt - 1 && y < x - 1 + kSnap; y++)
                 if (rend[y] == 0) return y + 1;
             return x;
         };
-        const int jb = snap(gid * chunk);
-        const int je = snap((gid + 1) * chunk);
-
+        auto process = [&](const int jb, const int je) {
         for (int pass = 0; pass < passes; pass++) {
             const int c0 = pass * Rc;  // first column of this pass
             const uint32_t loff = (uint32_t)(c0 + gl * VEC) * (uint32_t)sizeof(FT);
@@ -345,6 +349,24 @@ __global__ void __launch_bounds__(kThreads, FacCfg<NT, FT>::MinBlocks) k_mttkrp_
                     }
                 }
             }
+        }
+        };
+        for (int round = 0;; round++) {  // one place that runs process(), so it is compiled once
+            int x0, x1, ch;
+            if (G == 32) {
+                int ci = 0;
+                if (lane == 0) ci = atomicAdd(&next_chunk, 1);
+                ci = __shfl_sync(0xffffffffu, ci, 0);
+                ch = kChunk;
+                x0 = ci * kChunk;
+                x1 = min(x0 + kChunk, nt);
+            } else {
+                ch = (nt + ngroups - 1) / ngroups;
+                x0 = round == 0 ? gid * ch : nt;
+                x1 = (gid + 1) * ch;
+            }
+            if (x0 >= nt) break;
+            process(snap_to(x0, ch), snap_to(x1, ch));
         }
         __syncthreads();  // records and end levels are rewritten by the next tile
     }
