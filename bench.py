@@ -52,11 +52,10 @@ NUM_SMS = 152
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": "1bb54f54a7d88b13dab5c6586d0d00386a72b7108903cba587af786ed68f96b5",
+NCU_TRAFFIC = {"sha256": "7a82d25fbfe93b948e248dff4f22ecaea46891adb9cf3fafa2137c29571f6468",
                # full-size 1-pass capture (dram__bytes_read.sum + dram__bytes_write.sum)
-               # of the 4 per-mode launches of the FP64 factored MTTKRP: 19.93 / 18.34
-               # / 17.28 / 16.16 GB, their mean
-               "bytes_per_launch": 17.93e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
+               # of the 4 per-mode launches of the FP64 factored MTTKRP, their mean
+               "bytes_per_launch": 17.90e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
 
 
 # L1 / L2 traffic of the MTTKRP kernels from ncu captures of smaller cases of
@@ -64,16 +63,16 @@ NCU_TRAFFIC = {"sha256": "1bb54f54a7d88b13dab5c6586d0d00386a72b7108903cba587af78
 # per launch over the modes), scaled to a launch of the timed workload by its
 # nonzero count: the cache traffic of a launch is proportional to its
 # nonzeros. Filled from profiles/k_mttkrp_cache_traffic.md.
-_SHA_CACHE = "1bb54f54a7d88b13dab5c6586d0d00386a72b7108903cba587af786ed68f96b5"
+_SHA_CACHE = "7a82d25fbfe93b948e248dff4f22ecaea46891adb9cf3fafa2137c29571f6468"
 NCU_CACHE = [
     {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "f64", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
-     "nnz": 30e6, "l1_bytes": 4.455e10, "l2_bytes": 3.724e10},
+     "nnz": 30e6, "l1_bytes": 4.493e10, "l2_bytes": 3.732e10},
     {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "f32", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
      "nnz": 30e6, "l1_bytes": 2.413e10, "l2_bytes": 1.424e10},
     {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "bf16", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
-     "nnz": 30e6, "l1_bytes": 1.280e10, "l2_bytes": 7.761e9},
+     "nnz": 30e6, "l1_bytes": 1.280e10, "l2_bytes": 7.749e9},
     {"sha256": _SHA_CACHE, "family": "zipf3d-200Kx200Kx5K", "dtype": "f32", "workload": "zipf3d-200Kx200Kx5K-20M",
-     "nnz": 20e6, "l1_bytes": 5.255e9, "l2_bytes": 2.006e9},
+     "nnz": 20e6, "l1_bytes": 5.255e9, "l2_bytes": 2.007e9},
 ]
 
 
