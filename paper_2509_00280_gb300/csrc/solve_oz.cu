@@ -23,12 +23,16 @@
 // the order of FP64's own dot-product error bound (gamma_R sum_r |m_ir w_rs|),
 // plus the final rounding.
 //
-// Layout: W's 8 slices (B operand, N = 64 columns x K) are staged once per
-// block; per 128-row tile the 8 slices of M (A operand, M = 128 x K) are
-// staged (K-major core matrices, tcgen05.cuh), then per 32-column half of
-// the output 8 x 8 x K/16 MMAs of M = 128, N = 32, K = 16 fill the 15 group
-// accumulators (480 tensor-memory columns) and 8 warps drain them. The tile
-// is read completely before its rows are overwritten (in place).
+// Layout: W's 8 slices (B operand) are staged once per block, per 32-column
+// half of the output and 16-wide K chunk one 256-row block whose row 32 v + j
+// is slice v of output column j, so that one MMA of M = 128, N = 256, K = 16
+// forms the pairs (u, 0..7) of slice u of a row tile into the 8 consecutive
+// group accumulators u..u+7 (32 tensor-memory columns each, 480 in all; the
+// groups 8..14 are zeroed first by one MMA of a zero operand). Per 128-row
+// tile the 8 slices of M (A operand, M = 128 x K) are staged (K-major core
+// matrices, tcgen05.cuh); per half 1 + 8 K/16 MMAs, then 8 warps drain the
+// groups. The tile is read completely before its rows are overwritten (in
+// place).
 #include "internal.cuh"
 #include "slices.cuh"
 #include "tcgen05.cuh"
@@ -44,9 +48,10 @@ constexpr int SO_ROWS = 128;
 constexpr int SO_S = 8;                           // slices per entry
 constexpr int SO_GROUPS = 2 * SO_S - 1;           // g = u + v in 0..14
 constexpr int SO_MBLK = SO_ROWS * 16 * 2;         // one slice of one 16-wide K chunk of the tile: 4 KB
-constexpr int SO_WBLK = 64 * 16 * 2;              // one slice of one K chunk of W: 2 KB
+constexpr int SO_WBLK = 256 * 16 * 2;             // one K chunk of one 32-column half of W, all 8 slices: 8 KB
 constexpr int SO_MBYTES = SO_S * 4 * SO_MBLK;     // 128 KB
-constexpr int SO_WBYTES = SO_S * 4 * SO_WBLK;     // 64 KB
+constexpr int SO_WBYTES = 2 * 4 * SO_WBLK;        // 64 KB
+constexpr int SO_ZBYTES = SO_ROWS * 16 * 2;        // a zero A operand (128 x 16): 4 KB
 constexpr int SO_BLOCKS = 152;
 constexpr uint32_t SO_TMEM_COLS = 512;
 
@@ -91,7 +96,8 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
                long long wait_cycles, int fault_skip) {
     extern __shared__ __align__(1024) unsigned char smem_so[];
     unsigned char *sm = smem_so;               // M slices: [slice][chunk] 4 KB blocks
-    unsigned char *sw = smem_so + SO_MBYTES;   // W slices: [slice][chunk] 2 KB blocks
+    unsigned char *sw = smem_so + SO_MBYTES;   // W slices: [half][chunk] 8 KB blocks of 256 N rows
+    unsigned char *sz = sw + SO_WBYTES;        // zeros
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     __shared__ int gave_up;
@@ -107,16 +113,22 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
     __syncthreads();
     for (int x = tid; x < R * R; x += SO_THREADS) atomicMax(&wexp[x % R], expo_of(W[x]));
     __syncthreads();
-    for (int x = tid; x < 64 * 64; x += SO_THREADS) {  // (n = s, k = r), zero outside R x R
+    // B operand of half h, chunk c: N row n = 32 v + j is slice v of output column 32 h + j, so one
+    // N = 256 MMA forms the pairs (u, 0..7) of a slice u of M into 8 consecutive groups
+    for (int x = tid; x < 64 * 64; x += SO_THREADS) {  // (s, k = r), zero outside R x R
         const int s = x >> 6, r = x & 63;
         uint32_t u[SO_S];
         const double w = (s < R && r < R) ? W[r * R + s] : 0.0;
         slices8(w, s < R ? wexp[s] : 0, u);
-        const uint32_t off = (uint32_t)((s >> 3) * 256 + ((r & 15) >> 3) * 128 + (s & 7) * 16 + (r & 7) * 2);
+        unsigned char *blk = sw + (size_t)((s >> 5) * 4 + (r >> 4)) * SO_WBLK;
 #pragma unroll
-        for (int k = 0; k < SO_S; k++)
-            *reinterpret_cast<uint16_t *>(sw + (size_t)(k * 4 + (r >> 4)) * SO_WBLK + off) = (uint16_t)u[k];
+        for (int k = 0; k < SO_S; k++) {
+            const int n = 32 * k + (s & 31);
+            *reinterpret_cast<uint16_t *>(blk + (n >> 3) * 256 + ((r & 15) >> 3) * 128 + (n & 7) * 16 + (r & 7) * 2) =
+                (uint16_t)u[k];
+        }
     }
+    for (int x = tid; x < SO_ZBYTES / 4; x += SO_THREADS) reinterpret_cast<uint32_t *>(sz)[x] = 0u;
     if (warp == 0) tc::alloc(&tmem_base, SO_TMEM_COLS);
     if (tid == 0) {
         tc::mbar_init1(&bar);
@@ -127,7 +139,8 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = tc::instr_desc_bf16(128, 32);
+    const uint32_t idesc = tc::instr_desc_bf16(128, 256);
+    const uint32_t idesc_z = tc::instr_desc_bf16(128, 224);
     uint32_t phase = 0;
     bool stop = false;
 
@@ -174,21 +187,20 @@ __global__ void __launch_bounds__(SO_THREADS, 1)
             if (tid == 0 && !fault_skip) {
                 tc::fence_after();
                 // descriptors differ only in the start address field (address >> 4, below 2^14 for
-                // shared memory): offsets are added to two base descriptors
+                // shared memory): offsets are added to base descriptors
                 const uint64_t dm0 = tc::smem_desc(tc::saddr(sm), 128, 256);
-                const uint64_t dw0 = tc::smem_desc(tc::saddr(sw) + 1024u * (uint32_t)h, 128, 256);
+                const uint64_t dw0 = tc::smem_desc(tc::saddr(sw) + (uint32_t)(h * 4 * SO_WBLK), 128, 256);
+                // groups 8..14 (columns 256..479) start at zero: one MMA of a zero A operand
+                tc::mma(tmem + 256u, tc::smem_desc(tc::saddr(sz), 128, 256), dw0, idesc_z, 0u);
 #pragma unroll 1
                 for (int c = 0; c < KC; c++)
 #pragma unroll
                     for (int u = 0; u < SO_S; u++) {
+                        // pairs (u, v = 0..7) into groups u..u+7 (columns 32 u .. 32 u + 255); the first
+                        // MMA writes groups 0..7, every later one accumulates
                         const uint64_t da = dm0 + (uint64_t)(((u * 4 + c) * SO_MBLK) >> 4);
-#pragma unroll
-                        for (int v = 0; v < SO_S; v++) {
-                            const int g = u + v;
-                            const uint64_t db = dw0 + (uint64_t)(((v * 4 + c) * SO_WBLK) >> 4);
-                            const bool fresh = c == 0 && u == max(0, g - (SO_S - 1));
-                            tc::mma(tmem + 32u * (uint32_t)g, da, db, idesc, fresh ? 0u : 1u);
-                        }
+                        const uint64_t db = dw0 + (uint64_t)((c * SO_WBLK) >> 4);
+                        tc::mma(tmem + 32u * (uint32_t)u, da, db, idesc, (c == 0 && u == 0) ? 0u : 1u);
                     }
                 tc::commit(&bar);
             }
@@ -269,7 +281,7 @@ cudaError_t launch_solve_oz(double *M, int64_t I, int R, const double *W, int *e
     if (g > SO_BLOCKS) g = SO_BLOCKS;
     cudaError_t e = allow_max_dynamic_smem(k_solve_oz);
     if (e != cudaSuccess) return e;
-    k_solve_oz<<<(unsigned)g, SO_THREADS, SO_MBYTES + SO_WBYTES, st>>>(
+    k_solve_oz<<<(unsigned)g, SO_THREADS, SO_MBYTES + SO_WBYTES + SO_ZBYTES, st>>>(
         M, I, R, W, err, wait_cycles > 0 ? wait_cycles : kWaitCycles, fault_skip);
     return cudaGetLastError();
 }
