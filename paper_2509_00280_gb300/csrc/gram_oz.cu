@@ -23,9 +23,10 @@
 // summation's own typical error.
 //
 // Operands: two 64-row stages. Slice k of a 16-row chunk is a 2 KB block of
-// the K-major layout (tcgen05.cuh) holding the 64 columns as M rows, slices
-// i and i + S/2 adjacent so that one 4 KB M = 128 operand stacks them.
-// Entries with no data (columns >= R, rows past the end) are zero.
+// the K-major layout (tcgen05.cuh) holding the 64 columns as M rows, the 8
+// slices of a chunk in order, so that slices (a, a + 1) form one M = 128 A
+// operand and slices b.. one N = 128 or 256 B operand. Entries with no data
+// (columns >= R, rows past the end) are zero.
 #include <cmath>
 
 #include "internal.cuh"
@@ -44,7 +45,8 @@ constexpr int OZ_ITEMS = OZ_STAGE_ROWS / 2 * 64 / OZ_THREADS;  // (column, row p
 
 // two stages of slices, then the FP64 accumulators [half][column][row]
 // two stages of slices, then four 64-bit integer words per pair (r <= s) of the block's sums
-template <int S> constexpr size_t oz_smem_bytes() { return 2 * (size_t)S * OZ_CHUNKS * OZ_BLK + 4 * 2080 * 8; }
+// two stages of slices, a zero A operand (128 x 16 BF16), four 64-bit words per pair (r <= s)
+template <int S> constexpr size_t oz_smem_bytes() { return 2 * (size_t)S * OZ_CHUNKS * OZ_BLK + 4096 + 4 * 2080 * 8; }
 
 // Largest exponent field per column of a row-major I x R matrix (R <= 64),
 // atomicMax into colexp[0..R) (zeroed by the launcher). A warp walks rows,
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256) k_colexp(const double *__restrict__ A, in
 }
 
 // Drain of the tensor-memory blocks [C0, C1) of one pass: block c holds
-// group g = c + OFF (OFF = 0 in the lower 64 lanes, S / 2 in the upper 64).
+// group g = c + OFF (OFF = 0 in the lower 64 lanes, 1 in the upper 64).
 // Each FP32 value is an exact integer; the groups are combined exactly in
 // 64-bit words of four groups (word k = sum_{g = 4k..4k+3} acc_g
 // 2^(7 (4k + 3 - g)), so q_r q_s = sum_k word_k 2^(7 (11 - 4k))) and added
@@ -122,12 +124,13 @@ __device__ __forceinline__ void oz_drain(uint32_t tbase, unsigned long long *wor
 }
 
 // Per-block FP64 upper-triangle partials of A^T A (A: I x R row-major, R <=
-// 64), given colexp. With H = S / 2, the A operand of an MMA stacks slice i
-// (D lanes 0..63) over slice i + H (lanes 64..127), i < H, and the B operand
-// is slice j: one MMA forms the pairs (i, j) and (i + H, j) into tensor-memory
-// block i + j, whose lower lanes hold group i + j and upper lanes group
-// i + j + H. All S^2 pairs are formed (3H - 1 blocks; 8 at a time in 512
-// columns, so S = 8 takes a second pass over the staged slices), so the
+// 64), given colexp. One MMA stacks slices a (D lanes 0..63) and a + 1 (lanes
+// 64..127), a even, as the A operand and slices b.. (64 columns each) as the
+// B operand: it forms the pairs (a, b + n) and (a + 1, b + n) into tensor-
+// memory block a + b + n, whose lower lanes hold group a + b + n and upper
+// lanes group a + b + n + 1. The 64 pairs take 10 MMAs per 16-row chunk over
+// 14 blocks, 8 at a time in 512 columns, so a second pass re-reads the staged
+// slices; each pass's blocks are zeroed first by MMAs of a zero operand. The
 // products q_r q_s are exact and the only error is the truncation of q.
 // Per 128-row period: stage two 64-row buffers, MMAs, drain, per pass.
 // Waits on tensor-core commits give up after wait_cycles (then: err |= 2,
@@ -138,9 +141,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_gram_oz(const T *__restrict__ A, int64_t I, int R, const int *__restrict__ colexp, double *__restrict__ partial,
               int *__restrict__ err, long long wait_cycles, int fault_skip) {
     static_assert(S == 8, "8 slices: q exactly");
-    constexpr int H = S / 2;
-    constexpr int NCB = 3 * H - 1;                   // tensor-memory blocks of one period
-    constexpr int PA = NCB < 8 ? NCB : 8;            // blocks of the first pass
+    constexpr int NCB = 14;                          // tensor-memory blocks of one period (groups 0..14)
     constexpr int STAGE_BYTES = S * OZ_CHUNKS * OZ_BLK;
     constexpr uint32_t TMEM_COLS = 512;              // 8 blocks of 64 FP32 columns
     extern __shared__ __align__(1024) unsigned char smem_oz[];
@@ -148,7 +149,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __shared__ uint32_t tmem_base;
     __shared__ int gave_up;
     __shared__ int sE[64];
-    unsigned long long *words = reinterpret_cast<unsigned long long *>(smem_oz + 2 * (size_t)STAGE_BYTES);  // [k][pair]
+    unsigned char *zero_a = smem_oz + 2 * (size_t)STAGE_BYTES;  // a zero A operand
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(zero_a + 4096);  // [k][pair]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int npairs = R * (R + 1) / 2;
 
@@ -169,7 +171,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = tc::instr_desc_bf16(128, R <= 32 ? 32 : 64);
+    const uint32_t idesc256 = tc::instr_desc_bf16(128, 256), idesc128 = tc::instr_desc_bf16(128, 128);
+    for (int i = tid; i < 1024; i += OZ_THREADS) reinterpret_cast<uint32_t *>(zero_a)[i] = 0u;
 
     // drain roles: warp (lane quarter q, column half h) reads D lanes 32q..
     // (row r = 32 (q & 1) + lane of the lower (q < 2) or upper group set),
@@ -185,7 +188,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const bool mcol = m < R;
     const int Em = mcol ? sE[m] : 0;
     // byte offset of slice k of chunk c in a stage: slices i and i + H of a chunk are adjacent
-    auto blk = [](int k, int c) -> uint32_t { return (uint32_t)(((c * H + (k % H)) * 2 + k / H) * OZ_BLK); };
+    // byte offset of slice k of chunk c in a stage: the 8 slices of a chunk in order, 2 KB each
+    auto blk = [](int k, int c) -> uint32_t { return (uint32_t)((c * S + k) * OZ_BLK); };
 
     uint32_t phase = 0;
     bool stop = false;  // a wait gave up (the same in every thread)
@@ -223,29 +227,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
         __syncthreads();
 #pragma unroll 1
-        for (int pass = 0; pass < (NCB > 8 ? 2 : 1); pass++) {
-            const int c0 = pass == 0 ? 0 : 8, c1 = pass == 0 ? PA : NCB;
+        for (int pass = 0; pass < 2; pass++) {
             if (tid == 0) {
                 if (!fault_skip) {
                     tc::fence_after();
+                    // this pass's blocks start at zero: MMAs of the zero A operand (pass 0: blocks
+                    // 0..7, 512 columns; pass 1: blocks 8..13, 384 columns); every MMA below adds
+                    const uint64_t dz = tc::smem_desc(tc::saddr(zero_a), 128, 256);
+                    const uint64_t dany = tc::smem_desc(tc::saddr(smem_oz), 128, 256);
+                    tc::mma(tmem, dz, dany, idesc256, 0u);
+                    tc::mma(tmem + 256u, dz, dany, pass == 0 ? idesc256 : idesc128, 0u);
 #pragma unroll 1
                     for (int b = 0; b < 2; b++)
 #pragma unroll 1
-                        for (int c = 0; c < OZ_CHUNKS; c++)
-#pragma unroll
-                            for (int i = 0; i < H; i++) {
-                                // descriptors differ only in the start address field (address >> 4)
-                                const uint64_t d0 = tc::smem_desc(tc::saddr(smem_oz + (size_t)b * STAGE_BYTES), 128, 256);
-                                const uint64_t da = d0 + (uint64_t)(blk(i, c) >> 4);
-#pragma unroll
-                                for (int j = 0; j < S; j++) {
-                                    const int cb = i + j;
-                                    if (cb < c0 || cb >= c1) continue;
-                                    const uint64_t db = d0 + (uint64_t)(blk(j, c) >> 4);
-                                    const bool fresh = b == 0 && c == 0 && i == max(0, cb - (S - 1));
-                                    tc::mma(tmem + 64u * (uint32_t)(cb - c0), da, db, idesc, fresh ? 0u : 1u);
-                                }
+                        for (int c = 0; c < OZ_CHUNKS; c++) {
+                            // descriptors differ only in the start address field (address >> 4)
+                            const uint64_t d0 = tc::smem_desc(tc::saddr(smem_oz + (size_t)b * STAGE_BYTES), 128, 256);
+                            // A = slices (a, a + 1) stacked (D lanes 0..63 / 64..127), B = slices
+                            // b.. (N = 64 per slice): pairs (a, b + n) and (a + 1, b + n) into block
+                            // a + b + n, whose lower lanes hold group a + b + n, upper lanes the next
+                            auto mma = [&](int a, int bs, int nsl) {
+                                const int blk0 = a + bs - (pass == 0 ? 0 : 8);
+                                tc::mma(tmem + 64u * (uint32_t)blk0, d0 + (uint64_t)(blk(a, c) >> 4),
+                                        d0 + (uint64_t)(blk(bs, c) >> 4), nsl == 4 ? idesc256 : idesc128, 1u);
+                            };
+                            if (pass == 0) {  // blocks 0..7
+                                mma(0, 0, 4);
+                                mma(2, 0, 4);
+                                mma(4, 0, 4);
+                                mma(0, 4, 4);
+                                mma(6, 0, 2);
+                                mma(2, 4, 2);
+                            } else {          // blocks 8..13
+                                mma(4, 4, 4);
+                                mma(6, 4, 4);
+                                mma(6, 2, 2);
+                                mma(2, 6, 2);
                             }
+                        }
                     tc::commit(&bar);
                 }
             }
@@ -260,10 +279,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tc::fence_after();
             if (drainer) {
                 if (pass == 0) {
-                    if (upper) oz_drain<H, 0, PA>(tbase, words, npairs, rloc, 32 * hcol, R);
-                    else oz_drain<0, 0, PA>(tbase, words, npairs, rloc, 32 * hcol, R);
+                    if (upper) oz_drain<1, 0, 8>(tbase, words, npairs, rloc, 32 * hcol, R);
+                    else oz_drain<0, 0, 8>(tbase, words, npairs, rloc, 32 * hcol, R);
                 } else if constexpr (NCB > 8) {
-                    if (upper) oz_drain<H, 8, NCB>(tbase, words, npairs, rloc, 32 * hcol, R);
+                    if (upper) oz_drain<1, 8, NCB>(tbase, words, npairs, rloc, 32 * hcol, R);
                     else oz_drain<0, 8, NCB>(tbase, words, npairs, rloc, 32 * hcol, R);
                 }
             }
