@@ -16,7 +16,8 @@
 // magnitude <= 127^2, so over a 128-row period every partial sum is an integer
 // below 2^23 and the tensor cores add exactly. After each period the groups
 // are read back (tcgen05.ld), combined exactly in 64-bit integer words and
-// added to FP64 accumulators in shared memory; the result is scaled by
+// added to the block's 64-bit integer words of each pair in shared memory
+// (atomics, exact); the words are turned into FP64 and scaled by
 // 2^(E_r + E_s) once at the end. The products are exact; the truncation of
 // q (below 2^-55 of the column's largest magnitude per entry) bounds the
 // error of G_rs by 2^-53 sqrt(I) ||A(:, r)|| ||A(:, s)||, within FP64
