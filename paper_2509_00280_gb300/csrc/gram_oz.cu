@@ -44,8 +44,6 @@ constexpr int OZ_BLK = 2048;          // one slice of one 16-row chunk: 64 (M) x
 constexpr int OZ_BLOCKS = 152;
 constexpr int OZ_ITEMS = OZ_STAGE_ROWS / 2 * 64 / OZ_THREADS;  // (column, row pair) items per thread per stage
 
-// two stages of slices, then the FP64 accumulators [half][column][row]
-// two stages of slices, then four 64-bit integer words per pair (r <= s) of the block's sums
 // two stages of slices, a zero A operand (128 x 16 BF16), four 64-bit words per pair (r <= s)
 template <int S> constexpr size_t oz_smem_bytes() { return 2 * (size_t)S * OZ_CHUNKS * OZ_BLK + 4096 + 4 * 2080 * 8; }
 
