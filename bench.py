@@ -229,17 +229,26 @@ def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
     passes) and of each mode's hot-row count sort (4 passes), word packing,
     gather, partition statistics, per mode a histogram summary, a count and
     a hot-row list, and the 2-kernel norm;
-    CP-ALS = the initial Grams (partial + reduce per mode), one tile order per
-    SEGMENTED mode, and per iteration per mode: normal equations, MTTKRP,
-    then row pass + Gram (fused) + reduce + finish + store (FP32/FP64) or row
-    pass + 2 column-norm kernels + store + tensor-core Gram + reduce +
-    inner products (BF16), plus the fit and the kernel that records it."""
+    CP-ALS = the initial Grams, one tile order per SEGMENTED mode, and per
+    iteration per mode: normal equations, MTTKRP, then
+      FP64: tensor-core row pass, column exponents + tensor-core Gram +
+            reduce, finish, store (the initial Grams: exponents, Gram, reduce);
+      FP32 rows (FP32 factors, or BF16 with R % 8 != 0): row pass,
+            tensor-core Gram + reduce, finish, store;
+      BF16: row pass, 2 column-norm kernels, store, tensor-core Gram of the
+            stored factor + reduce, inner products;
+    plus the fit and the kernel that records it."""
     N = stats["nmodes"]
     passes = (stats["lp"] + 7) // 8
     encode = 1 + 5 * (passes + 4 * N) + 1 + 1 + 1 + 3 * N + 2
-    per_mode = 9 if (fdt == "bf16" and R % 8 == 0) else 6
+    if fdt == "f64":
+        per_mode, init = 8, 3
+    elif fdt == "bf16" and R % 8 == 0:
+        per_mode, init = 9, 2
+    else:
+        per_mode, init = 7, 2
     # graph replay with a fixed iteration count records each fit (1 kernel)
-    cpals = 2 * N + n_tile_orders + iters * (per_mode * N + 1 + 1)
+    cpals = init * N + n_tile_orders + iters * (per_mode * N + 1 + 1)
     return encode + cpals
 
 

@@ -1,8 +1,9 @@
 """Host-side arithmetic of bench.py (no GPU): the roofline's algorithmic bytes
 (the compulsory traffic of one mode-n MTTKRP: the stream once, each distinct
-row of the other factors once, the output once) and the per-step launch count
-(checked against an ncu launch list of the 50M-nonzero workload: 594 kernels
-per step without graph replay of fixed-count iterations, 619 with it)."""
+row of the other factors once, the output once), the per-step launch count
+(checked against an ncu launch list of the 150M-nonzero FP64 workload: 499
+kernels per step, 143 of them the encode) and the scaling of the cache
+traffic table."""
 import sys
 
 import pytest
@@ -30,10 +31,27 @@ def test_algorithmic_bytes_by_hand():
 def test_launch_count_matches_the_launch_list():
     # encode: key build, 5 kernels x (7 key passes + 3 x 4 count passes), words,
     # gather, statistics, 3 x (summary, count, hot rows), norm (2) = 110
-    # CP-ALS: 3 x 2 initial Gram kernels + 3 tile orders + 25 x (6 x 3 + fit + record)
-    assert bench._launches_per_step(STATS, 25, "f32", 3, 32) == 110 + 6 + 3 + 25 * 20
+    # CP-ALS FP32: 3 x 2 initial Gram kernels + 3 tile orders + 25 x (7 x 3 + fit + record)
+    assert bench._launches_per_step(STATS, 25, "f32", 3, 32) == 110 + 6 + 3 + 25 * 23
     bf16 = bench._launches_per_step(STATS, 10, "bf16", 3, 16)
     assert bf16 == 110 + 6 + 3 + 10 * (9 * 3 + 2)
+    # the 150M-nonzero 4-mode FP64 workload (l(p) = 65: 9 key passes), counted
+    # in its ncu launch list: encode 143; CP-ALS 4 x 3 initial Gram kernels,
+    # 4 tile orders, 10 x (8 x 4 + 2)
+    s4 = {"nmodes": 4, "lp": 65}
+    assert bench._launches_per_step(s4, 10, "f64", 4, 64) == 143 + 12 + 4 + 340 == 499
+
+
+def test_cache_rates_scale_with_nonzeros(monkeypatch):
+    sha = bench._kernel_sha()
+    monkeypatch.setattr(bench, "NCU_CACHE", [{"sha256": sha, "family": "fam-x", "dtype": "f64", "workload": "fam-x-1M",
+                                              "nnz": 1e6, "l1_bytes": 2e9, "l2_bytes": 1e9}])
+    r = bench._cache_rates("f64", "fam-x-5M", 5e6, 0.5)
+    assert abs(r["l1_gbs"] - 2e9 * 5 / 0.5 / 1e9) < 1e-9 and abs(r["l2_gbs"] - 1e9 * 5 / 0.5 / 1e9) < 1e-9
+    assert bench._cache_rates("f32", "fam-x-5M", 5e6, 0.5) is None      # other precision
+    assert bench._cache_rates("f64", "other-5M", 5e6, 0.5) is None      # other family
+    monkeypatch.setattr(bench, "NCU_CACHE", [dict(bench.NCU_CACHE[0], sha256="0" * 64)])
+    assert bench._cache_rates("f64", "fam-x-5M", 5e6, 0.5) is None      # counters of another kernel
 
 
 def test_kernel_sha_ignores_comments(tmp_path, monkeypatch):
