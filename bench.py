@@ -233,6 +233,9 @@ def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
     iteration per mode: normal equations, MTTKRP, then
       FP64: tensor-core row pass, column exponents + tensor-core Gram +
             reduce, finish, store (the initial Grams: exponents, Gram, reduce);
+            a mode with I R (3R + 1) / 2 <= 8e6 FMA runs its row pass and
+            Gram (partials + reduce) on the FP64 pipe instead, one kernel
+            fewer per update and per initial Gram;
       FP32 rows (FP32 factors, or BF16 with R % 8 != 0): row pass,
             tensor-core Gram + reduce, finish, store;
       BF16: row pass, 2 column-norm kernels, store, tensor-core Gram of the
@@ -242,13 +245,15 @@ def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
     passes = (stats["lp"] + 7) // 8
     encode = 1 + 5 * (passes + 4 * N) + 1 + 1 + 1 + 3 * N + 2
     if fdt == "f64":
-        per_mode, init = 8, 3
+        dims = stats.get("dims") or [1 << 62] * N
+        small = sum(1 for I in dims if I * R * (3 * R + 1) / 2 <= 8e6)
+        per_mode, init = 8 * N - small, 3 * N - small
     elif fdt == "bf16" and R % 8 == 0:
-        per_mode, init = 9, 2
+        per_mode, init = 9 * N, 2 * N
     else:
-        per_mode, init = 7, 2
+        per_mode, init = 7 * N, 2 * N
     # graph replay with a fixed iteration count records each fit (1 kernel)
-    cpals = init * N + n_tile_orders + iters * (per_mode * N + 1 + 1)
+    cpals = init + n_tile_orders + iters * (per_mode + 1 + 1)
     return encode + cpals
 
 

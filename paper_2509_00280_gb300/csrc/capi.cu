@@ -83,9 +83,10 @@ bool fault_is(const char *what) {
 // launch_gram with the gram_timeout test hook applied; a tensor-core wait
 // that runs out sets bit 1 of *err.
 cudaError_t gram_checked(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, int *err,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool cpals = false) {
     const bool f = fault_is("gram_timeout");
-    return launch_gram(A, I, R, dtype, scratch, G, err, st, f ? 100000000LL : 0, f ? 1 : 0);
+    return launch_gram(A, I, R, dtype, scratch, G, err, st, f ? 100000000LL : 0, f ? 1 : 0,
+                       cpals && !f && dense_f64_small(I, R));
 }
 
 template <typename T>
@@ -593,7 +594,7 @@ int run_mttkrp_batch(const BatchItemRef *items, int n, cudaStream_t st) {
 cudaError_t solve_checked(relate_handle_s *h, int64_t In, int R, cudaStream_t st) {
     const bool f = fault_is("gram_timeout");
     return launch_solve_rows(h->d_M, In, R, h->acc_dtype, h->d_Vinv, h->d_Vinv32, h->d_err, st, f ? 100000000LL : 0,
-                             f ? 1 : 0);
+                             f ? 1 : 0, !f && dense_f64_small(In, R));
 }
 
 bool tc_path_of(const relate_handle_s *h, int R) { return h->factor_dtype == RELATE_BF16 && gram_tc_supported(R); }
@@ -643,7 +644,7 @@ int mode_post(relate_handle_s *h, int R, int n, void *const *factors) {
     // have consumed V^{-1} and V: the next mode's normal equations may
     // overwrite them
     if ((e = solve_checked(h, In, R, st)) != cudaSuccess ||
-        (e = gram_checked(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, h->d_err, st)) != cudaSuccess ||
+        (e = gram_checked(h->d_M, In, R, h->acc_dtype, h->d_scratch, h->d_G + n * RR, h->d_err, st, true)) != cudaSuccess ||
         (e = launch_finish_mode(h->d_V, R, h->d_lambda, h->d_G + n * RR, h->d_inner, st)) != cudaSuccess)
         return cuda_fail(e, "relate_cpals: mode update");
     if (n + 1 < N && (e = fork_normal_eq(h, R, n + 1)) != cudaSuccess)
@@ -1060,7 +1061,7 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     }
     for (int k = 0; k < N; k++)
         if ((e = gram_checked(factors[k], (int64_t)h->dims[k], R, h->factor_dtype, h->d_scratch, h->d_G + k * RR,
-                              h->d_err, st)) != cudaSuccess)
+                              h->d_err, st, true)) != cudaSuccess)
             return cuda_fail(e, "relate_cpals: initial Gram");
     double prev = 0.0, fit = 0.0;
     int done = 0;
@@ -1269,7 +1270,7 @@ int relate_cpals_batch(relate_handle_t const *hs, int n, const int *R, int iters
         const int RR = R[p] * R[p];
         for (int k = 0; k < h->N; k++)
             if ((e = gram_checked(factors[p][k], (int64_t)h->dims[k], R[p], h->factor_dtype, h->d_scratch,
-                                  h->d_G + k * RR, h->d_err, st)) != cudaSuccess)
+                                  h->d_G + k * RR, h->d_err, st, true)) != cudaSuccess)
                 return cuda_fail(e, "relate_cpals_batch: initial Gram");
         if (!h->h_pinned && !(h->h_pinned = g_pinned.get()))
             return fail(RELATE_ERR_OOM, "relate_cpals_batch: pinned host words");

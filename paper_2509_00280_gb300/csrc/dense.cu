@@ -433,11 +433,13 @@ bool gram_uses_tc(const void *A, int R, int dtype) {
     return dtype == RELATE_BF16 && gram_tc_supported(R) && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
 }
 
+bool dense_f64_small(int64_t I, int R) { return (double)I * R * (3 * R + 1) / 2 <= 8e6; }
+
 cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, int *err,
-                        cudaStream_t st, long long wait_cycles, int fault_skip) {
+                        cudaStream_t st, long long wait_cycles, int fault_skip, bool simt_f64) {
     if (R < 1 || R > MAXR) return cudaErrorInvalidValue;
     if (I == 0) return cudaMemsetAsync(G, 0, sizeof(double) * R * R, st);
-    if (gram_uses_tc(A, R, dtype)) {
+    if (gram_uses_tc(A, R, dtype) && !(simt_f64 && dtype == RELATE_F64)) {
         // tcgen05 tensor cores: BF16 inputs directly, FP32 inputs as three
         // BF16 terms (gram_f32.cu), FP64 inputs as exact 7-bit slices (gram_oz.cu)
         const int npairs_tc = R * (R + 1) / 2;
@@ -491,12 +493,16 @@ static void solve_rows_rp(C *M, int64_t I, int R, const C *Vinv, int g, cudaStre
 }
 
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv, const float *Vinv32,
-                              int *err, cudaStream_t st, long long wait_cycles, int fault_skip) {
+                              int *err, cudaStream_t st, long long wait_cycles, int fault_skip, bool simt_f64) {
     if (I == 0) return cudaSuccess;
-    if (acc_dtype == RELATE_F64)  // tensor cores, exact integer slices (solve_oz.cu)
-        return launch_solve_oz((double *)M, I, R, Vinv, err, wait_cycles, fault_skip, st);
     int64_t g64 = (I + kThreads - 1) / kThreads;
     const int g = (int)(g64 > 152 * 8 ? 152 * 8 : g64);
+    if (acc_dtype == RELATE_F64) {
+        if (!simt_f64)  // tensor cores, exact integer slices (solve_oz.cu)
+            return launch_solve_oz((double *)M, I, R, Vinv, err, wait_cycles, fault_skip, st);
+        solve_rows_rp<double>((double *)M, I, R, Vinv, g, st);  // FP64 pipe
+        return cudaGetLastError();
+    }
     solve_rows_rp<float>((float *)M, I, R, Vinv32, g, st);
     return cudaGetLastError();
 }

@@ -225,7 +225,12 @@ size_t dense_scratch_doubles(int R);
 // gram_err_word) and NaN partials; wait_cycles <= 0 = kWaitCycles;
 // fault_skip (a test hook) issues no tensor-core work, so the waits run out.
 cudaError_t launch_gram(const void *A, int64_t I, int R, int dtype, double *scratch, double *G, int *err,
-                        cudaStream_t st, long long wait_cycles = 0, int fault_skip = 0);
+                        cudaStream_t st, long long wait_cycles = 0, int fault_skip = 0, bool simt_f64 = false);
+// FP64 dense steps small enough (I R (3R + 1) / 2 FMA <= 8e6, ~15 us on the
+// FP64 pipe) that the FP64-pipe kernels beat the tensor-core ones' fixed
+// costs (block setup, slicing of V^{-1}, several launches): CP-ALS passes
+// simt_f64 = true for them.
+bool dense_f64_small(int64_t I, int R);
 bool gram_uses_tc(const void *A, int R, int dtype);
 int *gram_err_word(double *scratch);
 
@@ -262,7 +267,7 @@ cudaError_t launch_normal_eq(const double *G_all, int N, int n, int R, double *V
 // FP32 on the FP32 pipe.
 cudaError_t launch_solve_rows(void *M, int64_t I, int R, int acc_dtype, const double *Vinv,
                               const float *Vinv32, int *err, cudaStream_t st, long long wait_cycles = 0,
-                              int fault_skip = 0);
+                              int fault_skip = 0, bool simt_f64 = false);
 // y[i] = (float)x[i], i < n.
 cudaError_t launch_to_float(const double *x, int n, float *y, cudaStream_t st);
 // In place M <- M W, FP64, R <= 64, as exact 7-bit integer slices on the

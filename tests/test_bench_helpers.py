@@ -40,6 +40,9 @@ def test_launch_count_matches_the_launch_list():
     # 4 tile orders, 10 x (8 x 4 + 2)
     s4 = {"nmodes": 4, "lp": 65}
     assert bench._launches_per_step(s4, 10, "f64", 4, 64) == 143 + 12 + 4 + 340 == 499
+    # its dims: only the 24-row mode is small enough for the FP64 pipe
+    s4d = dict(s4, dims=[5_000_000, 1_000_000, 100_000, 24])
+    assert bench._launches_per_step(s4d, 10, "f64", 4, 64) == 499 - 1 - 10
 
 
 def test_cache_rates_scale_with_nonzeros(monkeypatch):

@@ -1,7 +1,7 @@
 """The Gram on the tensor cores for FP64 inputs (exact integer slices of
 every entry, exact BF16 products, exact FP32 integer sums per 128-row period)
-and FP32 inputs (three BF16 terms per entry, FP32 accumulation per 2048
-rows).
+and FP32 inputs (three BF16 terms per entry, FP32 accumulation per 128
+rows, compensated FP32 sums across those periods).
 
 Inputs are k * 2^e with integer k of at most 26 (FP64) or 24 (FP32)
 significant bits and a per-row scale 2^e spread over 31 binades, so that the
@@ -13,8 +13,9 @@ reference has no error of its own. The bounds, relative to
 column's largest exponent, 2^-53 sqrt(I) (with a factor 2 of slack); a
 slicing that dropped the low-order pair products would be off by about
 I * 2^-53 on these inputs and fail the larger cases. FP32, the dropped terms
-of the three-term split (2^-22) plus FP32 summation over the rows one block
-accumulates before its FP64 drain (at most 2048; worst case linear in them).
+of the three-term split (2^-22) plus FP32 summation over the rows of one
+128-row period (worst case linear in them), plus the compensated sum of the
+periods (two more units of 2^-24).
 """
 import math
 
@@ -33,10 +34,10 @@ BITS = {"f64": 26, "f32": 24}
 def _bound(dt, I):
     if dt == "f64":
         return 2.0 * 2.0 ** -53 * math.sqrt(I)
-    # rows one block sums in FP32 before its FP64 drain: the launch takes
-    # min(152, ceil(I / 64)) blocks of ceil(I / blocks) rows
+    # rows one block sums plainly in FP32: the launch takes
+    # min(152, ceil(I / 64)) blocks of ceil(I / blocks) rows, in periods of 128
     blocks = min(152, max(1, -(-I // 64)))
-    return 2.0 ** -22 + min(-(-I // blocks), 2048) * 2.0 ** -24
+    return 2.0 ** -22 + (min(-(-I // blocks), 128) + 2) * 2.0 ** -24
 
 
 def _norm_err(G, ref):
