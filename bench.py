@@ -222,7 +222,20 @@ def _algorithmic_bytes(stats, mode, R, fb, ab, vb):
     return b
 
 
-def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
+def _kr_builds(kr_pairs):
+    """Khatri-Rao tables built per CP-ALS iteration: mode n's MTTKRP builds
+    its pair's table unless the last one built holds the same two modes and
+    neither was updated since (each iteration starts with none)."""
+    built, held = 0, None
+    for n, pair in enumerate(kr_pairs or []):
+        if pair is not None and tuple(pair) != held:
+            built, held = built + 1, tuple(pair)
+        if held is not None and n in held:
+            held = None  # A_n is rewritten after its MTTKRP
+    return built
+
+
+def _launches_per_step(stats, iters, fdt, n_tile_orders, R, kr_pairs=None):
     """Kernel launches of one step, counted from the library's launch
     sequence (and checked against an ncu launch list):
     encode = key build, 5 kernels per radix pass of the keys (ceil(l(p)/8)
@@ -240,7 +253,8 @@ def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
             tensor-core Gram + reduce, finish, store;
       BF16: row pass, 2 column-norm kernels, store, tensor-core Gram of the
             stored factor + reduce, inner products;
-    plus the fit and the kernel that records it."""
+    plus the fit and the kernel that records it, and per iteration the
+    Khatri-Rao table builds of fused modes (_kr_builds)."""
     N = stats["nmodes"]
     passes = (stats["lp"] + 7) // 8
     encode = 1 + 5 * (passes + 4 * N) + 1 + 1 + 1 + 3 * N + 2
@@ -253,7 +267,7 @@ def _launches_per_step(stats, iters, fdt, n_tile_orders, R):
     else:
         per_mode, init = 7 * N, 2 * N
     # graph replay with a fixed iteration count records each fit (1 kernel)
-    cpals = init + n_tile_orders + iters * (per_mode + 1 + 1)
+    cpals = init + n_tile_orders + iters * (per_mode + 1 + 1 + _kr_builds(kr_pairs))
     return encode + cpals
 
 
@@ -384,8 +398,11 @@ def _time_kernels(rl, torch, h, stream, d_fac, spec, R, fdt, dev, reps):
             torch.cuda.synchronize()
             if r:
                 ms.append(e0.elapsed_time(e1))
+        plan, kr = rl.relate_get_mode_plan(h, n, R), rl.relate_get_mode_kr(h, n, R)
+        d = plan["depth"]
         per_mode.append({"mode": n, "ms": statistics.mean(ms), "alg_bytes": _algorithmic_bytes(stats, n, R, fb, ab, vb),
-                         "alg_flops": spec.nnz * R * N, "strategy": rl.relate_get_conflict(h, n, R)})
+                         "alg_flops": spec.nnz * R * N, "strategy": rl.relate_get_conflict(h, n, R),
+                         "kr_pair": plan["level"][d - 1:d + 1] if kr["kr"] else None})
     return stats, per_mode
 
 
@@ -667,7 +684,7 @@ def main():
                        "final_fit": res["fit"]},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": _launches_per_step(stats, iters, fdt, sum(1 for m in per_mode if m["strategy"] == 2),
-                                               R) * args.steps,
+                                               R, [m["kr_pair"] for m in per_mode]) * args.steps,
             "roofline": roof,
             "clocks": clk.summary()}
     if var_out:

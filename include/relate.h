@@ -303,6 +303,28 @@ int relate_set_mode_plan(relate_handle_t h, int mode, int depth, const int8_t *l
  * entries (nullable); depth, col_passes nullable. Errors: INVALID_ARG. */
 int relate_get_mode_plan(relate_handle_t h, int mode, int R, int *depth, int8_t *level, int *col_passes);
 
+/* Khatri-Rao pair of one mode's fiber-factored MTTKRP. The MTTKRP of Sec. 2.2
+ * multiplies the unfolded tensor by the Khatri-Rao product of the other
+ * factors; with FP64 factors, a plan of depth >= 2 and one unfactored slot,
+ * the rows of A_a (.) A_b for a = level[depth - 1] and b = level[depth] (the
+ * last factored mode and the innermost one) are formed first, in a table of
+ * I_a * I_b rows of R values owned by the handle (device memory, grown on
+ * demand, at most 16 GiB and 2^32 rows), and every nonzero then gathers one
+ * table row and spends one FMA per element on those two modes: the level-a
+ * fiber closes (one multiply each) disappear. relate_mttkrp builds the table
+ * on every call (one more kernel, included in its time); relate_cpals builds
+ * it once per iteration for the modes that share it. kr: -1 = AUTO (on when
+ * I_a * I_b <= nnz / 16), 0 = off, 1 = on where the plan allows it (else the
+ * mode runs unfused). Results differ from the unfused kernel by rounding only
+ * (A_a (.) A_b is rounded once to FP64). Host call. Errors: INVALID_ARG. No
+ * counterpart in the paper, whose kernels are on CPUs. */
+int relate_set_mode_kr(relate_handle_t h, int mode, int kr);
+
+/* 1 when `mode`'s MTTKRP at rank R fuses a Khatri-Rao pair (the plan and
+ * the AUTO rule resolved), else 0; *rows: the table's rows (nullable).
+ * Errors: INVALID_ARG. */
+int relate_get_mode_kr(relate_handle_t h, int mode, int R, int *kr, uint64_t *rows);
+
 /* Changes the factor / accumulation dtypes used by later calls
  * (F64/F64, F32/F32 or BF16/F32): the precision forms of the factors and of
  * the MTTKRP accumulation; the encoding itself does not depend on them

@@ -15,8 +15,8 @@ from .relate import (  # noqa: F401
     RELATE_CONFLICT_SEGMENTED, RELATE_F32, RELATE_F64, RelateError, Handle, lib, library_path,
     relate_cpals, relate_decode, relate_encode, relate_footprint, relate_free, relate_get_conflict,
     relate_get_partitions, relate_get_stats, relate_gram, relate_gram_noalloc, relate_last_error, relate_solve_rows,
-    relate_get_mode_plan, relate_mttkrp, relate_mttkrp_batch, relate_cpals_batch, relate_release_cached_memory,
+    relate_get_mode_kr, relate_get_mode_plan, relate_mttkrp, relate_mttkrp_batch, relate_cpals_batch, relate_release_cached_memory,
     relate_set_conflict, relate_set_reduce_hook, relate_shard_range,
-    relate_set_cpals_graph, relate_set_mode_plan, relate_set_precision, relate_set_stream,
+    relate_set_cpals_graph, relate_set_mode_kr, relate_set_mode_plan, relate_set_precision, relate_set_stream,
     relate_status_string, relate_sync_status, relate_version,
 )

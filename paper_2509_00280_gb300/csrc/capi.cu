@@ -194,6 +194,15 @@ struct relate_handle_s {
     int8_t plan_level[kMaxModes][kMaxModes] = {};
     bool level_set[kMaxModes] = {};
     int plan_passes[kMaxModes] = {};
+    int plan_kr[kMaxModes] = {-1, -1, -1, -1, -1, -1, -1, -1};  // Khatri-Rao pair: -1 AUTO, 0 off, 1 on
+    // the Khatri-Rao rows of the last fused pair (grown on demand) and what
+    // they hold: modes (kr_a, kr_b) of factors (kr_fa, kr_fb) at rank kr_R;
+    // kr_valid is cleared whenever one of those factors may have changed
+    void *d_kr = nullptr;
+    size_t kr_bytes = 0;
+    int kr_a = -1, kr_b = -1, kr_R = 0;
+    const void *kr_fa = nullptr, *kr_fb = nullptr;
+    bool kr_valid = false;
     double *d_normX2 = nullptr;
     int *d_err = nullptr;  // device error flags of this handle's kernels
     uint64_t runs_n[kMaxModes] = {}, distinct[kMaxModes] = {}, maxcount[kMaxModes] = {};
@@ -232,7 +241,7 @@ struct relate_handle_s {
         if (ev_v) cudaEventDestroy(ev_v);
         if (h_pinned) g_pinned.put(h_pinned);
         void *ptrs[] = {d_words, d_vals, d_perm, d_plo, d_phi, d_normX2, d_err, d_M, d_scratch, d_G, d_Vinv,
-                        d_lambda, d_inner, d_fit, d_Vinv32, d_status, d_V, d_hot_scratch};
+                        d_lambda, d_inner, d_fit, d_Vinv32, d_status, d_V, d_hot_scratch, d_kr};
         for (void *p : ptrs)
             if (p) cudaFreeAsync(p, stream);
         for (auto *p : d_counts)
@@ -408,11 +417,26 @@ void fill_stream_args(const relate_handle_s *h, int mode, MttkrpArgs &a) {
 // the ones that miss in L2, are gathered once per outer fiber, and the
 // innermost slot (gathered per nonzero) is the shortest factor, which stays
 // in L1 or L2.
+//
+// Khatri-Rao pair: with FP64 factors (FP64-pipe bound), depth >= 2 and one
+// unfactored slot, the deepest level's mode a and the innermost mode b are
+// fused into one slot over the rows of A_a (.) A_b (the Khatri-Rao product of
+// the MTTKRP's definition, Sec. 2.2), built before the launch: each nonzero
+// then costs one FMA at that level instead of one plus one per closed level-a
+// fiber. AUTO fuses when the table has at most nnz / 16 rows (each row reused
+// 16 times on average, so its build and its gathers stay small against the
+// FMAs saved); on or off by relate_set_mode_kr.
 struct ModePlan {
     int depth;
     int8_t level[kMaxModes];
     int passes;
+    int kr;  // 1: fuse slots depth and depth + 1 (modes level[depth - 1], level[depth])
 };
+
+// Largest Khatri-Rao table: rows below 2^32 (32-bit record slots) and 16 GiB.
+constexpr uint64_t kKrMaxBytes = 16ull << 30;
+bool kr_fits(uint64_t rows, int R) { return rows < (1ull << 32) && rows * (uint64_t)R * 8 <= kKrMaxBytes; }
+bool kr_auto(uint64_t rows, int64_t nnz) { return rows * 16 <= (uint64_t)nnz; }
 
 ModePlan resolve_plan(const relate_handle_s *h, int mode, int R) {
     ModePlan p{};
@@ -447,6 +471,12 @@ ModePlan resolve_plan(const relate_handle_s *h, int mode, int R) {
     int bits = h->lbits[mode] + 11;
     for (int s = 0; s < p.depth; s++) bits += h->lbits[p.level[s]];
     while (p.depth > 0 && bits > 128) bits -= h->lbits[p.level[--p.depth]];
+    p.kr = 0;
+    if (h->factor_dtype == RELATE_F64 && p.depth >= 2 && h->N - 1 - p.depth == 1 && R % 2 == 0) {
+        const uint64_t rows = h->dims[p.level[p.depth - 1]] * h->dims[p.level[p.depth]];
+        const bool want = h->plan_kr[mode] >= 0 ? h->plan_kr[mode] == 1 : kr_auto(rows, h->nnz);
+        p.kr = want && kr_fits(rows, R) ? 1 : 0;
+    }
     return p;
 }
 
@@ -485,13 +515,63 @@ int ensure_tile_order(relate_handle_s *h, int mode, int R, cudaStream_t st, bool
 // The launch arguments of one mode's MTTKRP of the handle.
 void fill_run_args(relate_handle_s *h, int mode, void *const *factors, int R, void *out, MttkrpArgs &a);
 
-int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *out, cudaStream_t st) {
+// The Khatri-Rao table of the handle holds at least `bytes` (regrown outside
+// a capture only); false: not available now.
+bool ensure_kr(relate_handle_s *h, size_t bytes, cudaStream_t st) {
+    if (h->kr_bytes >= bytes && h->d_kr) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    if (h->d_kr) cudaFreeAsync(h->d_kr, st);
+    h->d_kr = nullptr;
+    h->kr_bytes = 0;
+    h->kr_valid = false;
+    if (dalloc(&h->d_kr, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        h->d_kr = nullptr;
+        return false;
+    }
+    h->kr_bytes = bytes;
+    return true;
+}
+
+// Bytes of the Khatri-Rao table mode `mode`'s plan fuses at rank R (0: none).
+size_t kr_plan_bytes(const relate_handle_s *h, const ModePlan &p, int R) {
+    if (!p.kr) return 0;
+    return (size_t)(h->dims[p.level[p.depth - 1]] * h->dims[p.level[p.depth]]) * R * 8;
+}
+
+// reuse_kr: the handle's Khatri-Rao rows may be kept when they hold the same
+// modes' factors (the caller clears kr_valid when one of them changes).
+int run_mttkrp(relate_handle_s *h, int mode, void *const *factors, int R, void *out, cudaStream_t st,
+               bool reuse_kr = false) {
     int rc0 = ensure_tile_order(h, mode, R, st);
     if (rc0) return rc0;
     MttkrpArgs a{};
     fill_run_args(h, mode, factors, R, out, a);
+    const ModePlan plan = resolve_plan(h, mode, R);
+    cudaError_t e;
+    const int ka = plan.kr ? plan.level[plan.depth - 1] : 0, kb = plan.kr ? plan.level[plan.depth] : 0;
+    // the table is built with 16-byte vector loads of both factors' rows
+    if (plan.kr && a.depth == plan.depth && reinterpret_cast<uintptr_t>(factors[ka]) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(factors[kb]) % 16 == 0 && ensure_kr(h, kr_plan_bytes(h, plan, R), st)) {
+        const bool keep = reuse_kr && h->kr_valid && h->kr_a == ka && h->kr_b == kb && h->kr_R == R &&
+                          h->kr_fa == factors[ka] && h->kr_fb == factors[kb];
+        if (!keep) {
+            if ((e = launch_kr_rows(factors[ka], factors[kb], h->dims[ka], h->dims[kb], R, h->factor_dtype, h->d_kr,
+                                    st)) != cudaSuccess)
+                return cuda_fail(e, "relate_mttkrp: Khatri-Rao rows");
+            h->kr_a = ka;
+            h->kr_b = kb;
+            h->kr_R = R;
+            h->kr_fa = factors[ka];
+            h->kr_fb = factors[kb];
+            h->kr_valid = true;
+        }
+        a.kr_table = h->d_kr;
+        a.kr_mul = (uint32_t)h->dims[kb];
+    }
     const int accb = mttkrp_acc_bytes(h->factor_dtype);
-    cudaError_t e = cudaMemsetAsync(out, 0, h->dims[mode] * (size_t)R * accb, st);
+    e = cudaMemsetAsync(out, 0, h->dims[mode] * (size_t)R * accb, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp memset");
     e = launch_mttkrp(a, h->KW, h->factor_dtype, h->val_dtype, h->smem_budget, h->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e, "relate_mttkrp launch");
@@ -621,6 +701,7 @@ int mode_pre(relate_handle_s *h, int R, int n) {
 // factor and its Gram, the fit's inner products.
 int mode_post(relate_handle_s *h, int R, int n, void *const *factors) {
     const cudaStream_t st = h->stream;
+    if (n == h->kr_a || n == h->kr_b) h->kr_valid = false;  // A_n is rewritten below
     const int N = h->N;
     const int RR = R * R;
     const int64_t In = (int64_t)h->dims[n];
@@ -675,8 +756,10 @@ int iteration_fit(relate_handle_s *h, int R, double *p_fit, int *p_stat, double 
 int cpals_iteration(relate_handle_s *h, int R, void *const *factors, double *p_fit, int *p_stat,
                     double *d_trace = nullptr, int *d_counter = nullptr) {
     int rc;
+    h->kr_valid = false;  // a captured iteration is replayed after other iterations changed every factor
     for (int n = 0; n < h->N; n++) {
-        if ((rc = mode_pre(h, R, n)) != RELATE_OK || (rc = run_mttkrp(h, n, factors, R, h->d_M, h->stream)) != RELATE_OK)
+        if ((rc = mode_pre(h, R, n)) != RELATE_OK ||
+            (rc = run_mttkrp(h, n, factors, R, h->d_M, h->stream, true)) != RELATE_OK)
             return rc;
         // sharded: the shards' partial MTTKRPs are summed before the update
         if (h->reduce_fn && h->reduce_fn(h->d_M, (int64_t)h->dims[n] * R, h->acc_dtype, h->stream, h->reduce_user) != 0)
@@ -1045,8 +1128,13 @@ int relate_cpals(relate_handle_t h, int R, int iters, double tol, void *const *f
     if (rc) return rc;
     const cudaStream_t st = h->stream;
     const int N = h->N;
-    for (int n = 0; n < N; n++)  // before any capture: tile orders are built once
+    size_t kr_need = 0;
+    for (int n = 0; n < N; n++) {  // before any capture: tile orders are built once
         if ((rc = ensure_tile_order(h, n, R, st)) != RELATE_OK) return rc;
+        const size_t b = kr_plan_bytes(h, resolve_plan(h, n, R), R);
+        kr_need = b > kr_need ? b : kr_need;
+    }
+    if (kr_need) ensure_kr(h, kr_need, st);  // else the modes run unfused
     const int RR = R * R;
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->d_status, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "relate_cpals: setup");
@@ -1501,6 +1589,24 @@ int relate_get_mode_plan(relate_handle_t h, int mode, int R, int *depth, int8_t 
     return RELATE_OK;
 }
 
+int relate_set_mode_kr(relate_handle_t h, int mode, int kr) {
+    g_err[0] = 0;
+    if (!h || mode < 0 || mode >= h->N || kr < -1 || kr > 1)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_set_mode_kr: bad argument");
+    h->plan_kr[mode] = kr;
+    return RELATE_OK;
+}
+
+int relate_get_mode_kr(relate_handle_t h, int mode, int R, int *kr, uint64_t *rows) {
+    g_err[0] = 0;
+    if (!h || mode < 0 || mode >= h->N || R < 1 || R > RELATE_MAX_RANK || !kr)
+        return fail(RELATE_ERR_INVALID_ARG, "relate_get_mode_kr: bad argument");
+    const ModePlan p = resolve_plan(h, mode, R);
+    *kr = p.kr;
+    if (rows) *rows = p.kr ? h->dims[p.level[p.depth - 1]] * h->dims[p.level[p.depth]] : 0;
+    return RELATE_OK;
+}
+
 int relate_set_precision(relate_handle_t h, relate_dtype_t factor_dtype, relate_dtype_t acc_dtype) {
     g_err[0] = 0;
     if (!h || !valid_precision(factor_dtype, acc_dtype))
@@ -1545,6 +1651,25 @@ int relate_footprint(const uint64_t *dims, int nmodes, int64_t nnz, const relate
     out->encode_peak = resident + temps;
     out->resident = resident;
     out->cpals_workspace = ws_total(maxI, nmodes, R);
+    if (p->factor_dtype == RELATE_F64 && nmodes >= 4 && nmodes <= 5 && R % 2 == 0) {
+        // the AUTO plans' Khatri-Rao table: the two shortest other modes
+        uint64_t kr = 0;
+        for (int m = 0; m < nmodes; m++) {
+            uint64_t s1 = ~0ull, s2 = ~0ull;  // the two smallest I_k, k != m
+            for (int k = 0; k < nmodes; k++) {
+                if (k == m) continue;
+                if (dims[k] < s1) {
+                    s2 = s1;
+                    s1 = dims[k];
+                } else if (dims[k] < s2) {
+                    s2 = dims[k];
+                }
+            }
+            const uint64_t rows = s1 * s2;
+            if (kr_auto(rows, nnz) && kr_fits(rows, R) && rows * R * 8 > kr) kr = rows * R * 8;
+        }
+        out->cpals_workspace += kr;
+    }
     out->factors = sumI * (uint64_t)R * dtype_bytes(p->factor_dtype);
     return RELATE_OK;
 }

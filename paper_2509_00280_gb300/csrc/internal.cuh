@@ -162,6 +162,14 @@ struct MttkrpArgs {
     int depth;
     int8_t level[kMaxModes];   // level[s - 1] = the mode in record slot s (s = 1..N-1)
     int col_passes;            // R split into this many column chunks, one walk of the records each
+    // Khatri-Rao pair of a fiber-factored mode with depth >= 2 and one
+    // unfactored slot (null = off): the rows of A_a (.) A_b for a = the
+    // deepest factored level's mode and b = the innermost mode, row
+    // i_a * kr_mul + i_b (kr_mul = I_b). launch_mttkrp then runs the kernel
+    // with those two slots as one, a level fewer: each nonzero gathers one
+    // product row and the level's fiber closes cost no multiply.
+    const void *kr_table;
+    uint32_t kr_mul;
     // record slot j of a decoded nonzero: slot 0 = the output mode, slots
     // 1..N-1 = the other modes in increasing order (filled by the launcher)
     int rshift[kMaxModes];
@@ -212,6 +220,11 @@ cudaError_t launch_mttkrp_batch(const MttkrpArgs *items, int n, int KW, int fact
 
 // Bytes of shared memory one row of the output accumulator takes.
 int mttkrp_acc_bytes(int factor_dtype);
+// out(ia * Ib + ib, :) = A(ia, :) * B(ib, :) elementwise, the rows of the
+// Khatri-Rao product A (.) B (FP64 or FP32, row-major with R columns, R even;
+// 16-byte aligned pointers; Ia * Ib < 2^32).
+cudaError_t launch_kr_rows(const void *A, const void *B, uint64_t Ia, uint64_t Ib, int R, int dtype, void *out,
+                           cudaStream_t st);
 
 // ---------------------------------------------------------------- dense
 // Scratch the dense kernels need (doubles): partial sums for the Gram and

@@ -92,6 +92,15 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
         a.S % 4 == 0 && a.R % V == 0) {
         // the fiber-factored kernel (mttkrp_fac.cuh): per-block copies of the
         // hot rows as for the SEGMENTED kernel
+        if (a.kr_table && a.kr_mul && a.depth >= 2 && a.N - 1 - a.depth == 1 &&
+            (reinterpret_cast<uintptr_t>(a.kr_table) % 16) == 0) {
+            // slots depth and depth + 1 as one slot over the Khatri-Rao rows
+            a.rfac[a.N - 2] = a.kr_table;
+            a.N -= 1;
+            a.depth -= 1;
+        } else {
+            a.kr_mul = 0;
+        }
         int hot = 0;
         a.full_copy = 0;
         if (a.hot_scratch && (size_t)a.In * a.R * accb <= kHotBlockBytes) {
@@ -173,6 +182,48 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a_in, int KW, int factor_dtype, int 
     case RELATE_F32: return mttkrp_f32(a, KW, vec_ok, acc_bytes, (int)grid, st);
     default: return mttkrp_bf16(a, KW, vec_ok, acc_bytes, (int)grid, st);
     }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_kr_rows(const T *__restrict__ A, const T *__restrict__ B, uint32_t Ib,
+                                                 uint32_t rows, int nv, T *__restrict__ out) {
+    constexpr int E = sizeof(V) / sizeof(T);
+    const int lane = threadIdx.x & 31;
+    const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t row = w0; row < rows; row += nw) {
+        const uint32_t ia = row / Ib, ib = row - ia * Ib;
+        for (int c = lane; c < nv; c += 32) {
+            const V x = reinterpret_cast<const V *>(A + (size_t)ia * nv * E)[c];
+            const V y = reinterpret_cast<const V *>(B + (size_t)ib * nv * E)[c];
+            V z;
+            const T *px = reinterpret_cast<const T *>(&x), *py = reinterpret_cast<const T *>(&y);
+            T *pz = reinterpret_cast<T *>(&z);
+#pragma unroll
+            for (int i = 0; i < E; i++) pz[i] = px[i] * py[i];
+            reinterpret_cast<V *>(out + (size_t)row * nv * E)[c] = z;
+        }
+    }
+}
+
+cudaError_t launch_kr_rows(const void *A, const void *B, uint64_t Ia, uint64_t Ib, int R, int dtype, void *out,
+                           cudaStream_t st) {
+    const uint64_t rows = Ia * Ib;
+    if (rows == 0) return cudaSuccess;
+    if (rows >= (1ull << 32) || R < 2 || R % 2 || (dtype != RELATE_F64 && dtype != RELATE_F32))
+        return cudaErrorInvalidValue;
+    const int threads = 256;
+    int64_t blocks = (int64_t)((rows + 7) / 8);  // 8 warps per block, a row per warp and step
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (dtype == RELATE_F64)
+        k_kr_rows<double, double2><<<(unsigned)blocks, threads, 0, st>>>(
+            (const double *)A, (const double *)B, (uint32_t)Ib, (uint32_t)rows, R / 2, (double *)out);
+    else if (R % 4 == 0)
+        k_kr_rows<float, float4><<<(unsigned)blocks, threads, 0, st>>>(
+            (const float *)A, (const float *)B, (uint32_t)Ib, (uint32_t)rows, R / 4, (float *)out);
+    else
+        k_kr_rows<float, float2><<<(unsigned)blocks, threads, 0, st>>>(
+            (const float *)A, (const float *)B, (uint32_t)Ib, (uint32_t)rows, R / 2, (float *)out);
+    return cudaGetLastError();
 }
 
 int tile_order_hot_rows(const MttkrpArgs &a) {

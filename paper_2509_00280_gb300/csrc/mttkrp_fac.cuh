@@ -14,6 +14,12 @@
 // the same terms as the flat loop's, in another association order (FP64:
 // rounding differences only).
 //
+// With a Khatri-Rao pair (MttkrpArgs::kr_table) the launcher hands this
+// kernel N - 1 slots and depth - 1 levels: the last slot then indexes the
+// rows of A_a (.) A_b of the deepest level's mode a and the innermost mode b,
+// so v * (A_a (.) A_b)(i_a, i_b) is summed straight into the next level out
+// (the tile order, sorted by mode a too, keeps those rows together).
+//
 // Layout as the SEGMENTED kernel: 2048-nonzero tiles staged by TMA, records
 // {value, i_n, i_p1, ..., i_p(N-1)} at their sorted positions from the
 // mode's precomputed tile order; per record the lowest slot at which it
@@ -234,6 +240,8 @@ __global__ void __launch_bounds__(kThreads, FacCfg<NT, FT>::MinBlocks) k_mttkrp_
             rec.val = a.vals_f64 ? (C)reinterpret_cast<const double *>(sv)[j] : (C)reinterpret_cast<const float *>(sv)[j];
 #pragma unroll
             for (int k = 0; k < NI; k++) rec.idx[k] = fld(w, a.rshift[k], a.rmask[k]);
+            if (a.kr_mul)  // the last slot indexes the Khatri-Rao rows of two modes
+                rec.idx[NI - 1] = rec.idx[NI - 1] * a.kr_mul + fld(w, a.rshift[NI], a.rmask[NI]);
             if (a.full_copy) rec.idx[0] |= 0x80000000u;  // every row has its slot: the row itself
             else if (hbin) rec.idx[0] = 0x80000000u | (hbin - 1u);
             *reinterpret_cast<R_t *>(srec + (size_t)p * RB) = rec;

@@ -84,6 +84,8 @@ def lib():
                 "relate_set_reduce_hook": (I, [P, P, P]),
                 "relate_cpals_batch": (I, [P, I, P, I, D, P, P, P, P, P]),
                 "relate_get_mode_plan": (I, [P, I, I, P, P, P]),
+                "relate_set_mode_kr": (I, [P, I, I]),
+                "relate_get_mode_kr": (I, [P, I, I, P, P]),
                 "relate_set_stream": (I, [P, P]),
                 "relate_set_cpals_graph": (I, [P, I]),
                 "relate_footprint": (I, [P, I, I64, P, I, P]),
@@ -332,6 +334,18 @@ def relate_get_mode_plan(h: Handle, mode: int, R: int) -> dict:
     _check(lib().relate_get_mode_plan(h.raw, int(mode), int(R), ctypes.byref(d), lv.ctypes.data, ctypes.byref(p)),
            "relate_get_mode_plan")
     return {"depth": d.value, "level": [int(x) for x in lv[:h.nmodes - 1]], "col_passes": p.value}
+
+
+def relate_set_mode_kr(h: Handle, mode: int, kr: int = -1) -> None:
+    """Khatri-Rao pair of one mode's factored MTTKRP (-1 AUTO, 0 off, 1 on)."""
+    _check(lib().relate_set_mode_kr(h.raw, int(mode), int(kr)), "relate_set_mode_kr")
+
+
+def relate_get_mode_kr(h: Handle, mode: int, R: int) -> dict:
+    k, rows = ctypes.c_int(0), ctypes.c_uint64(0)
+    _check(lib().relate_get_mode_kr(h.raw, int(mode), int(R), ctypes.byref(k), ctypes.byref(rows)),
+           "relate_get_mode_kr")
+    return {"kr": k.value, "rows": rows.value}
 
 
 def relate_set_precision(h: Handle, factor_dtype, acc_dtype=None) -> None:

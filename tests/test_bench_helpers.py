@@ -43,6 +43,11 @@ def test_launch_count_matches_the_launch_list():
     # its dims: only the 24-row mode is small enough for the FP64 pipe
     s4d = dict(s4, dims=[5_000_000, 1_000_000, 100_000, 24])
     assert bench._launches_per_step(s4d, 10, "f64", 4, 64) == 499 - 1 - 10
+    # modes 0 and 1 fuse the pair (2, 3): one table per iteration, reused by mode 1
+    assert bench._launches_per_step(s4d, 10, "f64", 4, 64, [[2, 3], [2, 3], None, None]) == 499 - 1
+    assert bench._kr_builds([[2, 3], [2, 3], [1, 3], None]) == 2
+    assert bench._kr_builds([[1, 2], None, None, [1, 2]]) == 2  # mode 1 rewrote A_1 in between
+    assert bench._kr_builds([[1, 2], [0, 2], None]) == 2        # another pair
 
 
 def test_cache_rates_scale_with_nonzeros(monkeypatch):

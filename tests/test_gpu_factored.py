@@ -154,3 +154,58 @@ def test_plan_validation():
     rl.relate_set_mode_plan(h, 0, 1, [2, 1], 1)
     assert rl.relate_get_mode_plan(h, 0, 8)["level"] == [2, 1]
     h.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3])
+def test_khatri_rao_pair_on_off(t4, n):
+    """The fused Khatri-Rao pair (relate_set_mode_kr): the deepest level's
+    mode and the innermost one as one slot over the rows of their Khatri-Rao
+    product (Sec. 2.2), against the oracle and against the unfused kernel."""
+    spec, c, v = t4
+    R = 32
+    h = encode_dev(c, v.astype(np.float64), spec.dims, factor_dtype="f64")
+    fs, dfs = _factors(spec.dims, R, "f64")
+    ref = oracle.mttkrp(c, v.astype(np.float64), spec.dims, n, fs)
+    rl.relate_set_conflict(h, n, SEG)
+    others = sorted((k for k in range(4) if k != n), key=lambda k: -spec.dims[k])
+    rows = spec.dims[others[1]] * spec.dims[others[2]]
+    got = rl.relate_get_mode_kr(h, n, R)
+    assert got == ({"kr": 1, "rows": rows} if rows * 16 <= spec.nnz else {"kr": 0, "rows": 0})
+    res = {}
+    for kr in (0, 1):
+        rl.relate_set_mode_kr(h, n, kr)
+        assert rl.relate_get_mode_kr(h, n, R)["kr"] == kr
+        res[kr] = _run(h, n, dfs, R, "f64")
+        assert rel_fro(res[kr], ref) <= 1e-12, (n, kr)
+    assert rel_fro(res[1], res[0]) <= 1e-13
+    # depth 1 leaves two unfactored slots: no pair to fuse
+    rl.relate_set_mode_plan(h, n, 1)
+    assert rl.relate_get_mode_kr(h, n, R)["kr"] == 0
+    assert rel_fro(_run(h, n, dfs, R, "f64"), ref) <= 1e-12
+    with pytest.raises(rl.RelateError):
+        rl.relate_set_mode_kr(h, n, 2)
+    h.close()
+
+
+def test_khatri_rao_pair_five_modes_and_factor_updates():
+    """Five modes at depth 3 (the kernel then runs 4 slots at depth 2); the
+    table is rebuilt on every relate_mttkrp call, so changed factors are seen."""
+    spec = synth.TensorSpec("kr5d", (3000, 2500, 400, 60, 30), 300_000,
+                            (("zipf", 1.2),) * 2 + (("uniform",),) * 3, values="uniform", value_dtype="f32", seed=57)
+    c, v = synth.make_tensor(spec)
+    R = 16
+    h = encode_dev(c, v.astype(np.float64), spec.dims, factor_dtype="f64")
+    fs, dfs = _factors(spec.dims, R, "f64")
+    for n in (0, 4):
+        rl.relate_set_conflict(h, n, SEG)
+        rl.relate_set_mode_kr(h, n, 1)
+        assert rl.relate_get_mode_kr(h, n, R)["kr"] == 1
+        ref = oracle.mttkrp(c, v.astype(np.float64), spec.dims, n, fs)
+        assert rel_fro(_run(h, n, dfs, R, "f64"), ref) <= 1e-12, n
+    # scale the innermost factor of mode 0's pair: the next call rebuilds the table
+    k = int(np.argmin([spec.dims[i] for i in range(1, 5)])) + 1
+    fs[k] = fs[k] * 3.0
+    dfs[k].mul_(3.0)
+    ref = oracle.mttkrp(c, v.astype(np.float64), spec.dims, 0, fs)
+    assert rel_fro(_run(h, 0, dfs, R, "f64"), ref) <= 1e-12
+    h.close()
