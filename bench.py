@@ -52,25 +52,28 @@ NUM_SMS = 152
 # DRAM traffic of the MTTKRP kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (sha256 of csrc/mttkrp_impl.cuh). None = not captured.
-NCU_TRAFFIC = {"sha256": "7a82d25fbfe93b948e248dff4f22ecaea46891adb9cf3fafa2137c29571f6468",
+NCU_TRAFFIC = {"sha256": "d0051ef187efbb77cb10433766bc0705194893553b17aade8d9238a0092e3e3e",
                # full-size 1-pass capture (dram__bytes_read.sum + dram__bytes_write.sum)
-               # of the 4 per-mode launches of the FP64 factored MTTKRP, their mean
-               "bytes_per_launch": 17.90e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
+               # of the 4 per-mode launches of the FP64 factored MTTKRP (modes 0-2 with
+               # their Khatri-Rao pairs), their mean
+               "bytes_per_launch": 28.66e9, "workload": "zipf4d-5Mx1Mx100Kx24-150M", "dtype": "f64"}
 
 
 # L1 / L2 traffic of the MTTKRP kernels from ncu captures of smaller cases of
 # the same workload families (l1tex__t_bytes.sum and lts__t_bytes.sum, mean
 # per launch over the modes), scaled to a launch of the timed workload by its
 # nonzero count: the cache traffic of a launch is proportional to its
-# nonzeros. Filled from profiles/k_mttkrp_cache_traffic.md.
-_SHA_CACHE = "7a82d25fbfe93b948e248dff4f22ecaea46891adb9cf3fafa2137c29571f6468"
+# nonzeros (the FP64 case captured with the Khatri-Rao pairs of modes 0-2 on,
+# as the AUTO plans of the 150M-nonzero case). Filled from
+# profiles/k_mttkrp_cache_traffic.md.
+_SHA_CACHE = "d0051ef187efbb77cb10433766bc0705194893553b17aade8d9238a0092e3e3e"
 NCU_CACHE = [
     {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "f64", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
-     "nnz": 30e6, "l1_bytes": 4.493e10, "l2_bytes": 3.732e10},
+     "nnz": 30e6, "l1_bytes": 3.472e10, "l2_bytes": 3.717e10},
     {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "f32", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
-     "nnz": 30e6, "l1_bytes": 2.413e10, "l2_bytes": 1.424e10},
+     "nnz": 30e6, "l1_bytes": 2.413e10, "l2_bytes": 1.425e10},
     {"sha256": _SHA_CACHE, "family": "zipf4d-5Mx1Mx100Kx24", "dtype": "bf16", "workload": "zipf4d-5Mx1Mx100Kx24-30M",
-     "nnz": 30e6, "l1_bytes": 1.280e10, "l2_bytes": 7.749e9},
+     "nnz": 30e6, "l1_bytes": 1.280e10, "l2_bytes": 7.759e9},
     {"sha256": _SHA_CACHE, "family": "zipf3d-200Kx200Kx5K", "dtype": "f32", "workload": "zipf3d-200Kx200Kx5K-20M",
      "nnz": 20e6, "l1_bytes": 5.255e9, "l2_bytes": 2.007e9},
 ]
@@ -477,6 +480,8 @@ def main():
                     help="encode once and time only the per-mode MTTKRP launches (profiling runs)")
     ap.add_argument("--plan-depth", type=int, default=None,
                     help="with --only-kernel: fiber-factoring depth of every mode (relate_set_mode_plan)")
+    ap.add_argument("--plan-kr", type=int, default=-1, choices=(-1, 0, 1),
+                    help="with --only-kernel: Khatri-Rao pair of every mode (relate_set_mode_kr; -1 AUTO)")
     ap.add_argument("--col-passes", type=int, default=0,
                     help="with --only-kernel: column passes of every mode (relate_set_mode_plan)")
     ap.add_argument("--only-dense", action="store_true",
@@ -544,6 +549,8 @@ def main():
             for n in range(N):
                 rl.relate_set_mode_plan(h, n, -1 if args.plan_depth is None else args.plan_depth, None,
                                         args.col_passes)
+        for n in range(N):
+            rl.relate_set_mode_kr(h, n, args.plan_kr)
         accdt = torch.float64 if fdt == "f64" else torch.float32
         ms = []
         for n in range(N):
@@ -557,7 +564,7 @@ def main():
                 torch.cuda.synchronize()
                 t.append(e0.elapsed_time(e1))
             ms.append(round(min(t), 3))
-        plans = [rl.relate_get_mode_plan(h, n, R) for n in range(N)]
+        plans = [dict(rl.relate_get_mode_plan(h, n, R), kr=rl.relate_get_mode_kr(h, n, R)) for n in range(N)]
         h.close()
         print(json.dumps({"only_kernel": spec.name, "modes": N, "launches_per_mode": max(1, args.steps),
                           "factor_dtype": fdt, "ms_per_mode_min": ms, "plans": plans}))

@@ -314,7 +314,7 @@ int relate_get_mode_plan(relate_handle_t h, int mode, int R, int *depth, int8_t 
  * fiber closes (one multiply each) disappear. relate_mttkrp builds the table
  * on every call (one more kernel, included in its time); relate_cpals builds
  * it once per iteration for the modes that share it. kr: -1 = AUTO (on when
- * I_a * I_b <= nnz / 16), 0 = off, 1 = on where the plan allows it (else the
+ * I_a * I_b <= nnz / 4), 0 = off, 1 = on where the plan allows it (else the
  * mode runs unfused). Results differ from the unfused kernel by rounding only
  * (A_a (.) A_b is rounded once to FP64). Host call. Errors: INVALID_ARG. No
  * counterpart in the paper, whose kernels are on CPUs. */

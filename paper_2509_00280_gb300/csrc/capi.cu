@@ -423,9 +423,11 @@ void fill_stream_args(const relate_handle_s *h, int mode, MttkrpArgs &a) {
 // fused into one slot over the rows of A_a (.) A_b (the Khatri-Rao product of
 // the MTTKRP's definition, Sec. 2.2), built before the launch: each nonzero
 // then costs one FMA at that level instead of one plus one per closed level-a
-// fiber. AUTO fuses when the table has at most nnz / 16 rows (each row reused
-// 16 times on average, so its build and its gathers stay small against the
-// FMAs saved); on or off by relate_set_mode_kr.
+// fiber. AUTO fuses when the table has at most nnz / 4 rows (each row reused
+// 4 times on average): building a row costs about one FMA per element, and
+// on the 150M-nonzero 4-mode tensor even the 24M-row table of its 100K-row
+// mode cut that mode from 45.9 to 35.9 ms, build included. On or off by
+// relate_set_mode_kr.
 struct ModePlan {
     int depth;
     int8_t level[kMaxModes];
@@ -436,7 +438,7 @@ struct ModePlan {
 // Largest Khatri-Rao table: rows below 2^32 (32-bit record slots) and 16 GiB.
 constexpr uint64_t kKrMaxBytes = 16ull << 30;
 bool kr_fits(uint64_t rows, int R) { return rows < (1ull << 32) && rows * (uint64_t)R * 8 <= kKrMaxBytes; }
-bool kr_auto(uint64_t rows, int64_t nnz) { return rows * 16 <= (uint64_t)nnz; }
+bool kr_auto(uint64_t rows, int64_t nnz) { return rows * 4 <= (uint64_t)nnz; }
 
 ModePlan resolve_plan(const relate_handle_s *h, int mode, int R) {
     ModePlan p{};

@@ -170,9 +170,9 @@ def test_lambda_to_device_memory():
 @pytest.mark.parametrize("graph", [0, 1])
 def test_fp64_four_modes_with_khatri_rao_pairs(graph):
     """A 4-mode FP64 run whose modes 0 and 1 fuse the same Khatri-Rao pair
-    (modes 2 and 3): the table is built once per iteration by mode 0 and reused
-    by mode 1, then stale once modes 2 and 3 are updated. Fit trace, lambda
-    and factors as the 3-mode FP64 case, in the plain and the graph path."""
+    (modes 2 and 3) and mode 2 the pair (1, 3): mode 0 builds the table, mode 1
+    reuses it, mode 2 rebuilds it from the updated A_1. Fit trace, lambda and
+    factors as the 3-mode FP64 case, in the plain and the graph path."""
     spec = synth.TensorSpec("kr-cpals4d", (6000, 3000, 300, 20), 400_000, (("zipf", 1.1),) * 3 + (("uniform",),),
                             values="uniform", value_dtype="f32", seed=58)
     c, v = synth.make_tensor(spec)
@@ -181,7 +181,7 @@ def test_fp64_four_modes_with_khatri_rao_pairs(graph):
     fs = synth.init_factors(spec.dims, R, seed=2)
     ref = oracle.cpals(c, v, spec.dims, R, 6, 0.0, fs)
     h = encode_dev(c, v, spec.dims, factor_dtype="f64")
-    assert [rl.relate_get_mode_kr(h, n, R)["kr"] for n in range(4)] == [1, 1, 0, 0]
+    assert [rl.relate_get_mode_kr(h, n, R)["kr"] for n in range(4)] == [1, 1, 1, 0]
     rl.relate_set_cpals_graph(h, graph)
     dfs = factors_dev(fs, "f64")
     res = rl.relate_cpals(h, R, 6, 0.0, dfs)

@@ -170,7 +170,7 @@ def test_khatri_rao_pair_on_off(t4, n):
     others = sorted((k for k in range(4) if k != n), key=lambda k: -spec.dims[k])
     rows = spec.dims[others[1]] * spec.dims[others[2]]
     got = rl.relate_get_mode_kr(h, n, R)
-    assert got == ({"kr": 1, "rows": rows} if rows * 16 <= spec.nnz else {"kr": 0, "rows": 0})
+    assert got == ({"kr": 1, "rows": rows} if rows * 4 <= spec.nnz else {"kr": 0, "rows": 0})
     res = {}
     for kr in (0, 1):
         rl.relate_set_mode_kr(h, n, kr)

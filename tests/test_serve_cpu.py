@@ -154,6 +154,14 @@ def test_footprint_is_host_only_and_consistent():
     assert rl.relate_footprint((1000, 2000, 3000), 10_000, 64)["cpals_workspace"] > f32["cpals_workspace"]
     dev = rl.relate_footprint((1000, 1000, 1000), 1_000_000, 16, coords_on_device=True)
     assert small["encode_peak"] - dev["encode_peak"] == 1_000_000 * (3 * 4 + 4)
+    # FP64 factors, 4 modes: the AUTO plans' Khatri-Rao table (the two shortest
+    # other modes of a mode, I_a * I_b <= nnz / 4 rows) joins the workspace:
+    # 60000 rows (modes 1 and 3 for mode 2) at 400K nonzeros, 6000 (modes 2 and 3) at 100K
+    d4 = (6000, 3000, 300, 20)
+    ws = {(dt, z): rl.relate_footprint(d4, z, 16, factor_dtype=dt)["cpals_workspace"]
+          for dt in ("f64", "f32") for z in (100_000, 400_000)}
+    assert ws["f64", 400_000] - ws["f64", 100_000] == (60000 - 6000) * 16 * 8
+    assert ws["f32", 400_000] == ws["f32", 100_000]
     with pytest.raises(rl.RelateError):
         rl.relate_footprint((2 ** 33, 4), 10, 8)
     with pytest.raises(rl.RelateError):
