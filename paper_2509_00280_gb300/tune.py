@@ -272,18 +272,33 @@ class ModeConfig:
     depth: int = 0           # fiber-factoring levels (SEGMENTED, 3..5 modes)
     level: tuple | None = None  # order of the other modes (None = AUTO)
     col_passes: int = 1      # R-tile width = R / col_passes
+    kr: int = 0              # FP64: fuse the innermost two modes' Khatri-Rao pair (relate_set_mode_kr)
 
     def as_dict(self) -> dict:
         return {"strategy": self.strategy, "depth": self.depth,
                 "level": list(self.level) if self.level is not None else None, "col_passes": self.col_passes,
-                "rtile": None}
+                "kr": self.kr}
+
+
+# The library's limits of a Khatri-Rao table: rows below 2^32 and 16 GiB of FP64.
+KR_MAX_BYTES = 16 << 30
+
+
+def kr_fits(dims, level, depth, R) -> bool:
+    """The pair (level[depth - 1], level[depth]) of an FP64 plan can be fused."""
+    if depth < 2 or depth != len(level) - 1 or R % 2:  # one unfactored slot
+        return False
+    rows = int(dims[level[depth - 1]]) * int(dims[level[depth]])
+    return rows < 2 ** 32 and rows * R * 8 <= KR_MAX_BYTES
 
 
 def mode_configs(dims, mode: int, R: int, factor_dtype: str) -> list[ModeConfig]:
     """The kernel plans tune_modes tries for one mode: ATOMIC; PRIVATIZED when
     the output fits a block's shared memory; SEGMENTED flat and, for 3 to 5
     modes, at every fiber-factoring depth with the other modes longest first
-    or shortest first, with the whole row or half of it per pass (R-tile)."""
+    or shortest first, with the whole row or half of it per pass (R-tile);
+    FP64 plans of depth N - 2 also with their innermost Khatri-Rao pair fused
+    where its table fits."""
     N = len(dims)
     accb = 8 if factor_dtype == "f64" else 4
     vec = 2 if factor_dtype == "f64" else 4
@@ -297,8 +312,10 @@ def mode_configs(dims, mode: int, R: int, factor_dtype: str) -> list[ModeConfig]
         passes = [1] + ([2] if R % 2 == 0 and (R // 2) % vec == 0 else [])
         for depth in range(1, N - 1):
             for level in dict.fromkeys((longest, shortest)):
+                krs = [0, 1] if factor_dtype == "f64" and kr_fits(dims, level, depth, R) else [0]
                 for p in passes:
-                    out.append(ModeConfig(2, depth, level, p))
+                    for kr in krs:
+                        out.append(ModeConfig(2, depth, level, p, kr))
     return out
 
 
@@ -306,6 +323,7 @@ def apply_config(rl, h, mode: int, cfg: ModeConfig) -> None:
     rl.relate_set_conflict(h, mode, cfg.strategy)
     rl.relate_set_mode_plan(h, mode, cfg.depth if cfg.strategy == 2 else 0,
                             list(cfg.level) if cfg.level is not None else None, cfg.col_passes)
+    rl.relate_set_mode_kr(h, mode, cfg.kr)
 
 
 def tune_modes(h, dims, R: int, factor_dtype: str, factors, reps: int = 3, verbose: bool = False, stream=None,
@@ -345,6 +363,7 @@ def tune_modes(h, dims, R: int, factor_dtype: str, factors, reps: int = 3, verbo
 
         rl.relate_set_conflict(h, n, 0)
         rl.relate_set_mode_plan(h, n, -1, None, 0)
+        rl.relate_set_mode_kr(h, n, -1)
         t_auto = time_mode()
         best = (math.inf, None)
         for cfg in mode_configs(dims, n, R, factor_dtype):

@@ -86,12 +86,20 @@ def test_mode_configs_enumerate_the_kernel_plans():
     from paper_2509_00280_gb300 import tune
     dims = (5000, 1000, 100, 24)
     cfgs = tune.mode_configs(dims, 0, 64, "f64")
-    # ATOMIC, SEGMENTED flat, then depth 1..2 x 2 level orders x 2 R-tiles
+    # ATOMIC, SEGMENTED flat, then depth 1..2 x 2 level orders x 2 R-tiles, and
+    # at depth 2 the Khatri-Rao pair on and off where its table fits: (2, 3) has
+    # 2400 rows, (2, 1) 100000 (both fit)
     assert [c.strategy for c in cfgs[:2]] == [1, 2]
     fac = [c for c in cfgs if c.depth > 0]
-    assert len(fac) == 2 * 2 * 2
+    assert len(fac) == 2 * 2 * 2 + 2 * 2
     assert {c.level for c in fac} == {(1, 2, 3), (3, 2, 1)}
     assert {c.col_passes for c in fac} == {1, 2}
+    assert {(c.depth, c.kr) for c in fac} == {(1, 0), (2, 0), (2, 1)}
+    assert not any(c.kr for c in tune.mode_configs(dims, 0, 64, "f32"))
+    # the 24-row mode's pair (1, 2) has 1e11 rows, over 2^32
+    big = (5_000_000, 1_000_000, 100_000, 24)
+    assert not tune.kr_fits(big, (0, 1, 2), 2, 64) and tune.kr_fits(big, (0, 2, 3), 2, 64)
+    assert not any(c.kr for c in tune.mode_configs(big, 3, 64, "f64") if c.level == (0, 1, 2))
     # a 24-row output fits shared memory: PRIVATIZED is tried
     assert any(c.strategy == 3 for c in tune.mode_configs(dims, 3, 64, "f32"))
     # 3-mode tensors: one level; R = 12 in FP32 cannot be halved into whole 4-element vectors
