@@ -159,10 +159,14 @@ int relate_encode(const uint32_t *coords, const void *vals, const uint64_t *dims
  * a scalar path runs. The first call for a SEGMENTED mode also builds the
  * mode's tile order (one stream-ordered allocation and one kernel on
  * `stream`; skipped while `stream` is being captured, the kernel then sorts
- * each tile itself). Calls on one handle must be ordered (one stream, or
- * events): the SEGMENTED strategy keeps per-block copies of a skewed mode's
- * hottest rows in scratch owned by the handle. Errors: INVALID_ARG, OOM,
- * CUDA (launch failure). */
+ * each tile itself). An FP64 mode with a Khatri-Rao pair (relate_set_mode_kr)
+ * first builds the pair's table in device memory owned by the handle (grown
+ * by a stream-ordered allocation outside a capture; inside one, or when the
+ * allocation fails, the mode runs unfused). Calls on one handle must be
+ * ordered (one stream, or events): the SEGMENTED strategy keeps per-block
+ * copies of a skewed mode's hottest rows, and the pairs their table, in
+ * memory owned by the handle. Errors: INVALID_ARG, OOM, CUDA (launch
+ * failure). */
 int relate_mttkrp(relate_handle_t h, int mode, void *const *factors, int R, void *out,
                   void *stream);
 
